@@ -1,0 +1,336 @@
+"""Throughput of the MD hot path on GB300: particle-timesteps per second.
+
+One "step" is one leapfrog time step of the whole hot path: the fused force + integration
+kernel, the refresh criterion, and (when the criterion fires) cell binning, ordering, reorder and
+the neighbour-matrix rebuild.  Default workload: WCA fluid, fcc 100^3 = 4,000,000 atoms at
+density 0.8, T = 1, skin 0.4, FP32 pair forces with FP64 state and reductions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload wca4m|lj16m|batch512]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+
+Under torchrun (N > 1) every rank advances its own independent copy of the workload (the path has
+no exchange between replicas); value = atoms x steps over all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WCA_RC = 2.0 ** (1.0 / 6.0)
+WORKLOADS = {
+    # fcc n^3 cells, density, temperature, cutoff, skin
+    "wca4m": dict(ncell=100, rho=0.8, T=1.0, rc=WCA_RC, skin=0.4, desc="WCA fluid, fcc 100^3 = 4,000,000 atoms"),
+    "lj16m": dict(ncell=160, rho=0.8442, T=0.72, rc=2.5, skin=0.3, desc="LJ r_c=2.5 shifted, fcc 160^3 = 16,384,000 atoms"),
+    "batch512": dict(nrep=512, nmin=500, nmax=32000, rhomin=0.6, rhomax=0.9, T=1.0, rc=WCA_RC, skin=0.4,
+                     desc="512 WCA replicas, N ~ U{500..32000}, rho ~ U[0.6, 0.9]"),
+}
+METRIC = "particle-timesteps/s"
+UNIT = "particle-steps/s"
+DT = 0.005
+SEED = {"wca4m": 2, "lj16m": 3, "batch512": 4}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_inputs(name, rank=0):
+    from paper_2003_14061_gb300 import inputs
+    w = WORKLOADS[name]
+    seed = SEED[name] + 1000 * rank
+    if name == "batch512":
+        specs = inputs.replica_specs(w["nrep"], w["nmin"], w["nmax"], w["rhomin"], w["rhomax"], seed)
+        states = inputs.replica_states(specs, w["T"], seed)
+        x = np.concatenate([s[0] for s in states])
+        v = np.concatenate([s[1] for s in states])
+        return x, v, dict(n_rep=[s[0] for s in specs], boxes=np.stack([s[2] for s in states]))
+    x, box = inputs.fcc_lattice(w["ncell"], w["rho"])
+    v = inputs.maxwell(x.shape[0], w["T"], seed)
+    return x, v, dict(box=box)
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        else:
+            self.lines = []
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes_per_atom_step(mean_nbrs: float, precision: str = "mixed") -> float:
+    """Bytes the fused step must move per atom (W counted at its mean row length).
+
+    mixed: read pos32 16 + count 4 + W 4m + x 24 + v 24; write x 24 + v 24 + pos32 16.
+    """
+    if precision == "mixed":
+        return 132.0 + 4.0 * mean_nbrs
+    if precision == "fp32":
+        return 16 + 4 + 12 + 16 + 12 + 4.0 * mean_nbrs
+    return 32 + 4 + 24 + 24 + 24 + 24 + 32 + 4.0 * mean_nbrs
+
+
+def cpu_oracle_rate(x, v, box, rc, steps, threads):
+    """Particle-steps/s of the FP64 oracle on the given state (host cores)."""
+    import oracle
+    oracle.set_threads(threads)
+    p = oracle.pot(rc=rc)
+    t0 = time.perf_counter()
+    oracle.run(x, v, box, p, dt=DT, nsteps=steps, with_props=False)
+    dt = time.perf_counter() - t0
+    return x.shape[0] * steps / dt, dt
+
+
+def run_gb300(args, rank, world, local_rank):
+    import torch
+    from paper_2003_14061_gb300.system import MDSystem
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOADS[args.workload]
+    x, v, geo = make_inputs(args.workload, rank)
+    n = x.shape[0]
+    s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
+                 rebuild_rule="vmax", **geo)
+    if args.ctas_per_sm:
+        s.set_tuning(ctas_per_sm=args.ctas_per_sm)
+    stream = s.stream
+    # warm-up (also melts the lattice: timed steps see a fluid)
+    s.integrate(args.warmup)
+    torch.cuda.synchronize()
+    s.timing()                                  # reset counters
+    s.set_timing(True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        s.integrate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    phases = s.timing()
+    s.set_timing(False)
+    props = s.props()
+    mean_nbrs = float(np.average([p["mean_nbrs"] for p in props], weights=s.n_rep))
+    rebuilds = sum(p["rebuilds"] for p in props) / len(props)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_atoms = n * world
+    value = total_atoms * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the fused force + leapfrog step)
+    step_ms, step_calls, step_launches = phases["step"]
+    peak, peak_kind = load_peaks()
+    bpa = algorithmic_bytes_per_atom_step(mean_nbrs)
+    per_launch_ms = step_ms / max(step_calls, 1)
+    achieved = bpa * n / (per_launch_ms * 1e-3) / 1e9
+    launches = sum(p[2] for p in phases.values())
+
+    # end to end through the public API with host buffers: pinned H2D of the state, K steps each
+    # followed by a D2H read of that step's props, and a D2H read of the final state
+    e2e_steps = min(args.steps, args.e2e_steps)
+    xh = torch.from_numpy(x).pin_memory()
+    vh = torch.from_numpy(v).pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    vo = torch.empty_like(vh).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(xh, vh)
+    for _ in range(e2e_steps):
+        s.integrate(1)
+        s.props()
+    s.state_into(xo, vo)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = total_atoms * e2e_steps / e2e_s
+    import ctypes  # noqa: F401  (md_props size)
+    from paper_2003_14061_gb300 import binding as B
+    props_bytes = ctypes.sizeof(B.md_props) * s.nrep
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            threads = os.cpu_count() or 1
+            if args.workload == "batch512":
+                from paper_2003_14061_gb300 import inputs
+                specs = inputs.replica_specs(8, 500, 32000, 0.6, 0.9, SEED["batch512"])
+                sts = inputs.replica_states(specs, 1.0, SEED["batch512"])
+                atoms, secs = 0, 0.0
+                for xs, vs, bs in sts:
+                    r, dtt = cpu_oracle_rate(xs, vs, bs, w["rc"], 10, threads)
+                    atoms += xs.shape[0] * 10
+                    secs += dtt
+                rate, sample = atoms / secs, "first 8 replicas of the batch recipe, 10 steps each"
+            else:
+                steps_cpu = args.cpu_steps
+                rate, _ = cpu_oracle_rate(x, v, geo["box"], w["rc"], steps_cpu, threads)
+                sample = f"{steps_cpu} steps of the full {n}-atom system from its initial state"
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "atoms_per_gpu": n, "precision": "FP32 pair forces, FP64 state",
+                       "skin": w["skin"], "rc": w["rc"], "dt": DT, "reorder_every": 100,
+                       "rebuild_rule": "max-velocity bound > skin/2",
+                       "l2": "inputs larger than L2 (state %.2f GB)" % (s.workspace_bytes / 1e9),
+                       "mean_neighbours": mean_nbrs, "rebuilds_per_100_steps": None},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_step<MD_MIXED>",
+                         "bytes_per_atom": bpa, "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 48.0 * total_atoms / e2e_steps,
+                    "d2h_bytes_per_step": props_bytes + 48.0 * total_atoms / e2e_steps, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "phases_ms": {k: round(vv[0], 3) for k, vv in phases.items()},
+            "phase_launches": {k: vv[2] for k, vv in phases.items()},
+        }
+    s.close()
+    return result
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on a bounded sample of the same workload (host cores)."""
+    import oracle
+    from paper_2003_14061_gb300 import inputs
+    w = WORKLOADS[args.workload]
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    p = oracle.pot(rc=w["rc"])
+    # calibrate the per-atom-step cost on a small system of the same recipe
+    rho = w.get("rho", 0.75)
+    xc, bc = inputs.fcc_lattice(16, rho)
+    vc = inputs.maxwell(xc.shape[0], w["T"], 1)
+    t0 = time.perf_counter()
+    oracle.run(xc, vc, bc, p, dt=DT, nsteps=2, with_props=False)
+    per = (time.perf_counter() - t0) / (2 * xc.shape[0])
+    budget = args.ref_seconds
+    natoms = budget / max(per * (args.steps + args.warmup), 1e-12)
+    full = 4 * w["ncell"] ** 3 if "ncell" in w else 8_300_000
+    ncell = max(6, min(int((min(natoms, full) / 4.0) ** (1.0 / 3.0)), w.get("ncell", 10 ** 6)))
+    x, box = inputs.fcc_lattice(ncell, rho)
+    v = inputs.maxwell(x.shape[0], w["T"], SEED[args.workload])
+    x, v, _, _ = oracle.run(x, v, box, p, dt=DT, nsteps=args.warmup, with_props=False)
+    t0 = time.perf_counter()
+    oracle.run(x, v, box, p, dt=DT, nsteps=args.steps, with_props=False)
+    secs = time.perf_counter() - t0
+    value = x.shape[0] * args.steps / secs
+    sample = f"fcc {ncell}^3 = {x.shape[0]} atoms of the same recipe, {args.steps} steps"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "atoms": x.shape[0]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=300)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="wca4m", choices=list(WORKLOADS))
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_gb300(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

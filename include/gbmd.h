@@ -1,0 +1,218 @@
+/*
+ * gbmd.h -- C ABI of libgbmd.so, a GB300 (sm_103a) library for short-range pair-force molecular
+ * dynamics with cell and neighbour lists in periodic boxes.
+ *
+ * The method is the one of Rapaport, "GPU molecular dynamics: Algorithms and performance"
+ * (arXiv 2003.14061): atoms are assigned to cells and cell layers (Sec. 2.3, steps N1-N4), a
+ * neighbour matrix W is built from the 27 surrounding cells (N5), forces are accumulated per atom
+ * from W without Newton's third law (F1), the energy is a reduction of per-atom terms (F2), the
+ * state is advanced by the leapfrog integrator (Sec. 4.3 item 1), W is refreshed when the maximum
+ * velocity says atoms may have moved by half the shell (Sec. 2.3), and atoms are periodically
+ * reordered by cell (Sec. 2.4 item 4, Sec. 4.1 item 1).
+ *
+ * Conventions
+ *   - Every function returns an int: MD_OK (0) or a negative md_status.  Nothing throws across
+ *     this boundary.  md_last_error() gives a message for the last failure on this thread.
+ *   - Device memory: the caller allocates one workspace of md_workspace_bytes() bytes (device
+ *     memory, 256-byte aligned) and passes it to md_create / md_create_batch; the library carves
+ *     all its arrays out of it and allocates nothing else on the device.  The caller frees the
+ *     workspace after md_destroy.
+ *   - Host arrays passed in are owned by the caller and are only read or written during the call.
+ *     Pointers named "host or device" may point to either (unified addressing decides).
+ *   - Streams: every call is ordered on the stream given at creation (a cudaStream_t passed as
+ *     void*).  Only md_reduce_props, md_get_state, md_get_cells, md_get_neighbours, md_check and
+ *     md_adjoint wait for the stream; the others return after queueing work.
+ *   - Atoms carry permanent ids 0..n-1 (the order of the arrays given at creation), which survive
+ *     reordering (Sec. 4.1 item 1).  All state exchanged through this ABI is in id order.
+ *   - Errors detected on the device (neighbour-capacity overflow, non-finite values) are latched
+ *     in device memory and returned by the next call that waits for the stream.
+ */
+#ifndef GBMD_H
+#define GBMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_system md_system;   /* opaque; owned by the library */
+
+/* Arithmetic of the pair forces and of the state (Sec. 4.1 item 7 discusses s.p. and d.p.).
+ *   MD_FP64  : pair forces, positions and velocities in FP64.
+ *   MD_MIXED : pair forces in FP32; positions, velocities and all reductions beyond a 32-lane
+ *              warp in FP64.
+ *   MD_FP32  : pair forces, positions and velocities in FP32; reductions in FP64. */
+typedef enum { MD_FP64 = 0, MD_MIXED = 1, MD_FP32 = 2 } md_precision;
+
+/* When the neighbour matrix is rebuilt (Sec. 2.3: "the maximal atom velocity needed to determine
+ * when the neighbor matrix needs rebuilding").
+ *   MD_REBUILD_VMAX  : D += dt * max_i |v_i| after every position update; rebuild when
+ *                      D > skin/2, then D = 0.
+ *   MD_REBUILD_DISP  : rebuild when max_i |x_i - x_i(at last rebuild)| > skin/2.
+ *   MD_REBUILD_EVERY : rebuild before every force evaluation (a plain cell list when skin = 0). */
+typedef enum { MD_REBUILD_VMAX = 0, MD_REBUILD_DISP = 1, MD_REBUILD_EVERY = 2 } md_rebuild_rule;
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID_ARG = -1,   /* bad pointer, size or parameter */
+    MD_ERR_BOX_TOO_SMALL = -2, /* fewer than 3 cells of side >= r_c + skin along an axis */
+    MD_ERR_NBR_OVERFLOW = -3,  /* an atom had more neighbours than nbr_capacity */
+    MD_ERR_CELL_OVERFLOW = -4, /* more than 1023 cells along an axis, or too many atoms */
+    MD_ERR_NONFINITE = -5,     /* a non-finite position, velocity or force was produced */
+    MD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+    MD_ERR_CUDA = -7,          /* a CUDA runtime call failed */
+    MD_ERR_WORKSPACE = -8      /* workspace missing, misaligned or smaller than required */
+} md_status;
+
+/* Parameters shared by all replicas of a system (the paper keeps them in one constant-memory
+ * struct, Sec. 2.4 item 2).  Lengths in units of sigma, energies of eps, masses of m. */
+typedef struct {
+    int64_t n;             /* atoms (md_create); ignored by md_create_batch */
+    double box[3];         /* periodic box sides (md_create); ignored by md_create_batch */
+    double eps;            /* Lennard-Jones epsilon */
+    double sigma;          /* Lennard-Jones sigma */
+    double mass;           /* atom mass */
+    double rc;             /* interaction cutoff r_c (absolute; WCA: 2^(1/6) sigma) */
+    double skin;           /* neighbour shell thickness delta (Sec. 4.1 item 5); 0 = cell list */
+    double dt;             /* time step */
+    int32_t shift_energy;  /* 1: u(r) shifted so that u(r_c) = 0 (the forces are unchanged) */
+    int32_t precision;     /* md_precision */
+    int32_t reorder_every; /* reorder atoms by cell at the first rebuild at least this many steps
+                              after the last reorder (Sec. 4.1 item 1: 100); 0 = every rebuild */
+    int32_t nbr_capacity;  /* rows of W, i.e. maximum neighbours per atom; 0 = automatic */
+    int32_t rebuild_rule;  /* md_rebuild_rule */
+    int32_t props_every;   /* >0: accumulate props every this many steps inside md_integrate into
+                              a device time series (md_get_series); 0: only on md_reduce_props */
+} md_params;
+
+/* Measured quantities of one replica (Sec. 2.3: total interaction energy from the reduction of
+ * the u_i, kinetic energy, maximal velocity), plus the virial and pressure. */
+typedef struct {
+    double U;              /* potential energy sum_{i<j} u(r_ij) = (1/2) sum_i u_i */
+    double K;              /* kinetic energy (m/2) sum_i |v_i|^2, velocities at the integer step */
+    double E_per_atom;     /* (U + K) / n */
+    double virial;         /* W = sum_{i<j} r_ij . f_ij */
+    double pressure;       /* (2K + W) / (3V) */
+    double P[3];           /* total momentum m sum_i v_i */
+    double vmax;           /* max_i |v_i| */
+    double mean_nbrs;      /* mean neighbour count at the last rebuild */
+    int64_t step;          /* steps taken since creation or md_set_state */
+    int64_t rebuilds;      /* neighbour-matrix rebuilds since creation or md_set_state */
+    int32_t max_cell_occ;  /* N_l = max_c k_c at the last rebuild (Sec. 2.3 step N3) */
+    int32_t max_nbrs;      /* max_i m_i at the last rebuild */
+} md_props;
+
+/* Size of the workspace for one system (md_create) or a batch (md_create_batch); 0 on error. */
+size_t md_workspace_bytes(const md_params* p);
+size_t md_workspace_bytes_batch(const md_params* p, int32_t nrep, const int64_t* n_rep,
+                                const double* box_rep);
+
+/* Create one system of p->n atoms in box p->box.  x0, v0: host or device, [n][3] FP64 in id
+ * order; positions are wrapped into the box.  The call bins the atoms, reorders them by cell and
+ * builds the neighbour matrix (N1-N5).  stream: cudaStream_t (NULL = legacy default stream). */
+int md_create(const md_params* p, void* d_workspace, size_t workspace_bytes, const double* x0,
+              const double* v0, void* stream, md_system** out);
+
+/* Create nrep independent systems advanced together (Sec. 4.3 item 2: independent simulations
+ * carried out simultaneously in a single run).  n_rep[r] atoms, box_rep[3r..3r+2]; x0/v0 hold
+ * the replicas' atoms concatenated in replica order ([sum n_rep][3], FP64, host or device).
+ * Replica r's atoms have ids sum_{q<r} n_rep[q] + 0 .. n_rep[r]-1. */
+int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, const double* box_rep,
+                    void* d_workspace, size_t workspace_bytes, const double* x0, const double* v0,
+                    void* stream, md_system** out);
+
+/* N1-N4 (Sec. 2.3) and the reorder of Sec. 2.4 item 4: bin every atom into its cell, count the
+ * cell occupancies k_c, prefix-sum them and list each cell's atoms in ascending slot order; if a
+ * reorder is due (or reorder_every == 0), permute the atoms into that order. */
+int md_bin_cells(md_system* s);
+
+/* N5 (Sec. 2.3): rebuild the neighbour matrix W from the current binning.  Each W entry holds the
+ * neighbour's slot and its cell's periodic offset; neighbours are within r_c + skin by the
+ * FP32 (MD_MIXED, MD_FP32) or FP64 (MD_FP64) criterion on cell-local coordinates. */
+int md_build_neighbours(md_system* s);
+
+/* F1 (Sec. 2.3): forces f_i and per-atom energies u_i at the current positions from W, without
+ * advancing the state (read them with md_get_state). */
+int md_compute_forces(md_system* s);
+
+/* Advance every replica by nsteps leapfrog steps (kick-drift-kick, Sec. 4.3 item 1), evaluating
+ * forces from W each step and rebuilding W (with a reorder when due) whenever the rebuild rule
+ * fires.  Stream-ordered; does not wait. */
+int md_integrate(md_system* s, int32_t nsteps);
+
+/* F2 (Sec. 2.3) and the other measured quantities at the current state, one md_props per replica
+ * (out must hold md_nrep(s) entries; host pointer).  Waits for the stream. */
+int md_reduce_props(md_system* s, md_props* out);
+
+/* Time series written by md_integrate when props_every > 0: up to max_rows rows of
+ * [step, U, K, W, P, px, py, pz, vmax] (9 doubles) per replica, replica-major, oldest first.
+ * Returns the number of rows written per replica through *rows.  Host pointer.  Waits. */
+int md_get_series(md_system* s, double* out, int32_t max_rows, int32_t* rows);
+int md_clear_series(md_system* s);
+
+/* State in id order.  x: positions wrapped into the box; v: velocities at the current integer
+ * step; f: forces at the current positions (computed by this call).  Each may be NULL; host or
+ * device; [n_total][3] FP64.  Waits for the stream. */
+int md_get_state(md_system* s, double* x, double* v, double* f);
+
+/* Replace positions and velocities (id order, [n_total][3] FP64, host or device), resetting the
+ * step and rebuild counters, then bin, reorder and rebuild W as md_create does. */
+int md_set_state(md_system* s, const double* x, const double* v);
+
+/* Diagnostics in id order (host pointers), from the last binning / rebuild:
+ *   md_get_cells      : cell[n_total] = linear cell id (c_z n_y + c_y) n_x + c_x in the replica.
+ *   md_get_neighbours : counts[n_total] = m_i; nbr_ids[n_total * cap] = the neighbours' ids
+ *                       (row i, first counts[i] entries, unordered; rows truncated at cap). */
+int md_get_cells(md_system* s, int32_t* cell);
+int md_get_neighbours(md_system* s, int32_t* counts, int32_t* nbr_ids, int32_t cap);
+
+/* Waits for the stream and returns the first latched device error (then clears it). */
+int md_check(md_system* s);
+
+/* Sizes: replicas, total atoms, rows of W, cells per axis of replica r (nc[3]). */
+int32_t md_nrep(const md_system* s);
+int64_t md_natoms(const md_system* s);
+int32_t md_nbr_capacity(const md_system* s);
+int md_cells_per_axis(const md_system* s, int32_t r, int32_t* nc);
+
+/* Launch shapes chosen by the autotuner (threads per block of the step and build kernels,
+ * persistent CTAs per SM).  0 keeps the current value. */
+typedef struct {
+    int32_t step_block;      /* 64..1024, multiple of 32 */
+    int32_t build_block;     /* 64..1024, multiple of 32 */
+    int32_t ctas_per_sm;     /* persistent grid size = SMs * ctas_per_sm */
+    int32_t use_graph;       /* 1: replay md_integrate from captured CUDA graphs */
+} md_tuning;
+int md_set_tuning(md_system* s, const md_tuning* t);
+int md_get_tuning(const md_system* s, md_tuning* t);
+
+/* Per-phase timing (the breakdown of Table 2 of the paper: neighbour matrix, forces +
+ * integration, layer/cell assignment, reorder, energy).  With timing enabled, every phase is
+ * bracketed by CUDA events on the system's stream.  md_get_timing waits for the stream, then
+ * returns for each phase the summed milliseconds (0 while timing is off), the number of times
+ * it was issued and the number of kernels launched, and resets the counters.  Arrays hold
+ * MD_NPHASE entries (host pointers, each may be NULL). */
+#define MD_NPHASE 6
+enum {
+    MD_PHASE_STEP = 0,     /* F1 fused with the leapfrog update (and F2 when props_every hits) */
+    MD_PHASE_BIN = 1,      /* N1-N4: cells, occupancy counts, prefix sum, cell order */
+    MD_PHASE_REORDER = 2,  /* reorder of the atoms by cell (Sec. 4.1 item 1) */
+    MD_PHASE_BUILD = 3,    /* N5: neighbour matrix */
+    MD_PHASE_PROPS = 4,    /* md_reduce_props: forces and reductions at the current state */
+    MD_PHASE_OTHER = 5     /* state exchange and standalone force passes */
+};
+int md_set_timing(md_system* s, int32_t enable);
+int md_get_timing(md_system* s, double* ms, int64_t* calls, int64_t* launches);
+
+/* Release the system (host-side bookkeeping and graphs).  The workspace stays the caller's. */
+int md_destroy(md_system* s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* md_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBMD_H */

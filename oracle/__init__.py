@@ -62,6 +62,7 @@ def _load():
         lib.orc_cells.argtypes = [i64, dp, dp, d, dp, dp]
         lib.orc_cell_order.argtypes = [i64, dp, i64, dp, dp]
         lib.orc_neighbours.argtypes = [i64, dp, dp, d, d, i32, dp, dp, dp, dp]
+        lib.orc_neighbours_sample.argtypes = [i64, dp, dp, d, d, i32, i64, dp, i64, dp, dp]
         lib.orc_props.argtypes = [i64, dp, dp, dp, P, d, dp]
         lib.orc_run.argtypes = [i64, dp, dp, dp, P, d, d, i64, i32, d, dp, dp]
         lib.orc_force_jvp.argtypes = [i64, dp, dp, P, dp, dp]
@@ -69,7 +70,7 @@ def _load():
         lib.orc_adjoint.argtypes = [i64, dp, dp, dp, P, d, d, i64, dp, dp, dp, dp, dp, dp]
         lib.orc_loss.argtypes = [i64, dp, dp, dp, P, d, d, i64, dp]
         for name in ("orc_forces_brute", "orc_forces_cells", "orc_force_on_atoms", "orc_cells",
-                     "orc_cell_order", "orc_neighbours", "orc_props", "orc_run", "orc_force_jvp",
+                     "orc_cell_order", "orc_neighbours", "orc_neighbours_sample", "orc_props", "orc_run", "orc_force_jvp",
                      "orc_param_grads", "orc_adjoint", "orc_loss"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
@@ -186,6 +187,19 @@ def neighbours(x, box, rc, skin, fp32: bool = True):
     _check(lib.orc_neighbours(n, _ptr(x), _ptr(box), float(rc), float(skin), int(fp32), _ptr(nc),
                               _ptr(counts2), _ptr(offsets), _ptr(nbrs)), "neighbours(fill)")
     return nc, counts, offsets, nbrs[: int(offsets[-1])]
+
+
+def neighbours_sample(x, box, rc, skin, atoms, cap, fp32: bool = True):
+    """Neighbour sets of the listed atoms: (counts [s], nbrs [s, cap] ascending, -1 padded)."""
+    x = _f64(x, (-1, 3))
+    box = _f64(box, (3,))
+    atoms = np.ascontiguousarray(atoms, dtype=np.int64)
+    counts = np.zeros(atoms.shape[0], dtype=np.int64)
+    nb = np.full((atoms.shape[0], int(cap)), -1, dtype=np.int64)
+    _check(_load().orc_neighbours_sample(x.shape[0], _ptr(x), _ptr(box), float(rc), float(skin), int(fp32),
+                                         atoms.shape[0], _ptr(atoms), int(cap), _ptr(counts), _ptr(nb)),
+           "neighbours_sample")
+    return counts, nb
 
 
 def props(x, v, box, p: Pot, mass=1.0):

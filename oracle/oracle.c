@@ -402,79 +402,118 @@ static int cmp_i64(const void* a, const void* b)
     return (x > y) - (x < y);
 }
 
-int orc_neighbours(int64_t n, const double* x, const double* box, double rc, double skin,
-                   int32_t use_fp32, int32_t* nc_out, int64_t* counts, const int64_t* offsets,
-                   int64_t* nbrs)
+/* Neighbours of atom i under the criterion above; writes up to cap of them (ascending) to out
+ * and returns the full count. */
+static int64_t orc_nbrs_of_atom(const orc_cell_list* cl, const double* loc, const double w[3],
+                                const float wf[3], double rl2, float rl2f, int32_t use_fp32,
+                                int64_t i, int64_t* out, int64_t cap)
 {
-    if (n < 0 || !x || !box || !nc_out || !counts) return ORC_ERR_ARG;
-    double rl = rc + skin;
-    orc_cell_list cl;
-    int rcode = orc_cell_list_build(n, x, box, rl, &cl);
+    int32_t ci[3];
+    orc_decode_cell(cl->cell[i], cl->nc, ci);
+    int64_t m = 0;
+    for (int oz = -1; oz <= 1; ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+    for (int ox = -1; ox <= 1; ++ox) {
+        int o[3] = {ox, oy, oz};
+        int32_t cx = (ci[0] + ox + cl->nc[0]) % cl->nc[0];
+        int32_t cy = (ci[1] + oy + cl->nc[1]) % cl->nc[1];
+        int32_t cz = (ci[2] + oz + cl->nc[2]) % cl->nc[2];
+        int64_t cc = ((int64_t)cz * cl->nc[1] + cy) * cl->nc[0] + cx;
+        for (int64_t k = cl->start[cc]; k < cl->start[cc + 1]; ++k) {
+            int64_t j = cl->order[k];
+            if (j == i) continue;
+            int inside;
+            if (use_fp32) {
+                float d[3];
+                for (int a = 0; a < 3; ++a) {
+                    float t = (float)loc[3 * j + a] - (float)loc[3 * i + a];
+                    float off = (float)o[a] * wf[a];
+                    d[a] = t + off;
+                }
+                float r2 = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+                inside = r2 < rl2f;
+            } else {
+                double d[3];
+                for (int a = 0; a < 3; ++a) {
+                    double t = loc[3 * j + a] - loc[3 * i + a];
+                    double off = (double)o[a] * w[a];
+                    d[a] = t + off;
+                }
+                double r2 = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
+                inside = r2 < rl2;
+            }
+            if (inside) {
+                if (out && m < cap) out[m] = j;
+                ++m;
+            }
+        }
+    }
+    if (out) qsort(out, (size_t)(m < cap ? m : cap), sizeof(int64_t), cmp_i64);
+    return m;
+}
+
+/* Cell list of side r_c + skin and the cell-local FP64 coordinates of every atom. */
+static int orc_nbr_setup(int64_t n, const double* x, const double* box, double rl, orc_cell_list* cl,
+                         double** loc_out, double w[3], float wf[3])
+{
+    int rcode = orc_cell_list_build(n, x, box, rl, cl);
     if (rcode) return rcode;
-    double w[3];
-    float wf[3];
-    for (int a = 0; a < 3; ++a) { w[a] = box[a] / (double)cl.nc[a]; wf[a] = (float)w[a]; }
-    double rl2 = rl * rl;
-    float rl2f = (float)rl2;
-    /* cell-local coordinates of every atom, from its cell */
+    for (int a = 0; a < 3; ++a) { w[a] = box[a] / (double)cl->nc[a]; wf[a] = (float)w[a]; }
     double* loc = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!loc) { orc_cell_list_free(&cl); return ORC_ERR_MEM; }
+    if (!loc) { orc_cell_list_free(cl); return ORC_ERR_MEM; }
     for (int64_t i = 0; i < n; ++i) {
         int32_t ci[3];
-        orc_decode_cell(cl.cell[i], cl.nc, ci);
+        orc_decode_cell(cl->cell[i], cl->nc, ci);
         for (int a = 0; a < 3; ++a) {
             double xa = orc_wrap(x[3 * i + a], box[a]);
             double origin = (double)ci[a] * w[a];
             loc[3 * i + a] = xa - origin;
         }
     }
+    *loc_out = loc;
+    return ORC_OK;
+}
+
+int orc_neighbours(int64_t n, const double* x, const double* box, double rc, double skin,
+                   int32_t use_fp32, int32_t* nc_out, int64_t* counts, const int64_t* offsets,
+                   int64_t* nbrs)
+{
+    if (n < 0 || !x || !box || !nc_out || !counts) return ORC_ERR_ARG;
+    double rl = rc + skin, w[3], *loc = NULL;
+    float wf[3];
+    orc_cell_list cl;
+    int rcode = orc_nbr_setup(n, x, box, rl, &cl, &loc, w, wf);
+    if (rcode) return rcode;
+    double rl2 = rl * rl;
+    float rl2f = (float)rl2;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        int32_t ci[3];
-        orc_decode_cell(cl.cell[i], cl.nc, ci);
-        int64_t m = 0;
-        int64_t base = (nbrs && offsets) ? offsets[i] : 0;
-        for (int oz = -1; oz <= 1; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-            int o[3] = {ox, oy, oz};
-            int32_t cx = (ci[0] + ox + cl.nc[0]) % cl.nc[0];
-            int32_t cy = (ci[1] + oy + cl.nc[1]) % cl.nc[1];
-            int32_t cz = (ci[2] + oz + cl.nc[2]) % cl.nc[2];
-            int64_t cc = ((int64_t)cz * cl.nc[1] + cy) * cl.nc[0] + cx;
-            for (int64_t k = cl.start[cc]; k < cl.start[cc + 1]; ++k) {
-                int64_t j = cl.order[k];
-                if (j == i) continue;
-                int inside;
-                if (use_fp32) {
-                    float d[3];
-                    for (int a = 0; a < 3; ++a) {
-                        float t = (float)loc[3 * j + a] - (float)loc[3 * i + a];
-                        float off = (float)o[a] * wf[a];
-                        d[a] = t + off;
-                    }
-                    float r2 = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
-                    inside = r2 < rl2f;
-                } else {
-                    double d[3];
-                    for (int a = 0; a < 3; ++a) {
-                        double t = loc[3 * j + a] - loc[3 * i + a];
-                        double off = (double)o[a] * w[a];
-                        d[a] = t + off;
-                    }
-                    double r2 = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
-                    inside = r2 < rl2;
-                }
-                if (inside) {
-                    if (nbrs && offsets) nbrs[base + m] = j;
-                    ++m;
-                }
-            }
-        }
-        counts[i] = m;
-        if (nbrs && offsets) qsort(&nbrs[base], (size_t)m, sizeof(int64_t), cmp_i64);
+        int64_t* out = (nbrs && offsets) ? &nbrs[offsets[i]] : NULL;
+        int64_t cap = (nbrs && offsets) ? offsets[i + 1] - offsets[i] : 0;
+        counts[i] = orc_nbrs_of_atom(&cl, loc, w, wf, rl2, rl2f, use_fp32, i, out, cap);
     }
     nc_out[0] = cl.nc[0]; nc_out[1] = cl.nc[1]; nc_out[2] = cl.nc[2];
+    free(loc);
+    orc_cell_list_free(&cl);
+    return ORC_OK;
+}
+
+/* Neighbour sets of the listed atoms only: counts[s] and nbrs[s * cap ..] (ascending, truncated). */
+int orc_neighbours_sample(int64_t n, const double* x, const double* box, double rc, double skin,
+                          int32_t use_fp32, int64_t nsample, const int64_t* atoms, int64_t cap,
+                          int64_t* counts, int64_t* nbrs)
+{
+    if (n < 0 || !x || !box || !atoms || !counts || !nbrs || cap <= 0) return ORC_ERR_ARG;
+    double rl = rc + skin, w[3], *loc = NULL;
+    float wf[3];
+    orc_cell_list cl;
+    int rcode = orc_nbr_setup(n, x, box, rl, &cl, &loc, w, wf);
+    if (rcode) return rcode;
+    double rl2 = rl * rl;
+    float rl2f = (float)rl2;
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < nsample; ++s)
+        counts[s] = orc_nbrs_of_atom(&cl, loc, w, wf, rl2, rl2f, use_fp32, atoms[s], &nbrs[s * cap], cap);
     free(loc);
     orc_cell_list_free(&cl);
     return ORC_OK;

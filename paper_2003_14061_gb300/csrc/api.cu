@@ -1,0 +1,658 @@
+// api.cu -- the C ABI of libgbmd.so (declared in include/gbmd.h): parameter checks, the plan of
+// slots / tiles / cells, the carving of the caller's workspace, and the host sequence of kernel
+// launches for each entry point.  No device memory is allocated here.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gbmd_internal.cuh"
+
+using namespace gbmd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define GBMD_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(MD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+struct Plan {
+    int32_t nrep = 0;
+    std::vector<Rep> reps;
+    std::vector<int32_t> tile_rep;
+    int64_t nslots = 0;
+    int32_t ntiles = 0;
+    int32_t ncells = 0;
+    int32_t nchunks = 0;
+    int32_t cap = 0;
+    int32_t series_cap = 0;
+    int64_t n_total = 0;
+    int mode = MD_MIXED;
+    int rule = MD_REBUILD_VMAX;
+};
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += std::max<size_t>(count, 1) * sizeof(T);
+        return p;
+    }
+};
+
+int check_params(const md_params* p)
+{
+    if (!p) return fail(MD_ERR_INVALID_ARG, "params is NULL");
+    auto pos = [](double x) { return std::isfinite(x) && x > 0.0; };
+    if (!pos(p->eps) || !pos(p->sigma) || !pos(p->mass) || !pos(p->rc) || !pos(p->dt))
+        return fail(MD_ERR_INVALID_ARG, "eps, sigma, mass, rc and dt must be finite and > 0");
+    if (!std::isfinite(p->skin) || p->skin < 0.0) return fail(MD_ERR_INVALID_ARG, "skin must be >= 0");
+    if (p->precision < MD_FP64 || p->precision > MD_FP32) return fail(MD_ERR_INVALID_ARG, "bad precision");
+    if (p->rebuild_rule < MD_REBUILD_VMAX || p->rebuild_rule > MD_REBUILD_EVERY)
+        return fail(MD_ERR_INVALID_ARG, "bad rebuild_rule");
+    if (p->reorder_every < 0 || p->nbr_capacity < 0 || p->props_every < 0)
+        return fail(MD_ERR_INVALID_ARG, "reorder_every, nbr_capacity and props_every must be >= 0");
+    return MD_OK;
+}
+
+int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const double* box_rep, Plan* P)
+{
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (nrep <= 0 || !n_rep || !box_rep) return fail(MD_ERR_INVALID_ARG, "need nrep > 0, n_rep and box_rep");
+    const double rl = p->rc + p->skin;
+    P->nrep = nrep;
+    P->mode = p->precision;
+    P->rule = p->rebuild_rule;
+    P->reps.resize(nrep);
+    int64_t slot = 0, cells = 0, ids = 0;
+    double rho_max = 0.0;
+    for (int32_t r = 0; r < nrep; ++r) {
+        Rep& R = P->reps[r];
+        std::memset(&R, 0, sizeof(R));
+        if (n_rep[r] <= 0) return fail(MD_ERR_INVALID_ARG, "every replica needs at least one atom");
+        int64_t nc_tot = 1;
+        for (int a = 0; a < 3; ++a) {
+            const double L = box_rep[3 * r + a];
+            if (!(std::isfinite(L) && L > 0.0)) return fail(MD_ERR_INVALID_ARG, "box sides must be > 0");
+            const double q = std::floor(L / rl);
+            if (q < 3.0)
+                return fail(MD_ERR_BOX_TOO_SMALL, "replica " + std::to_string(r) +
+                                                      ": fewer than 3 cells of side >= rc + skin");
+            if (q > MAX_NC) return fail(MD_ERR_CELL_OVERFLOW, "more than 1023 cells along an axis");
+            R.nc[a] = int32_t(q);
+            R.L[a] = L;
+            R.w[a] = L / double(R.nc[a]);
+            R.s[a] = double(R.nc[a]) / L;
+            R.wf[a] = float(R.w[a]);
+            nc_tot *= R.nc[a];
+        }
+        R.n = int32_t(n_rep[r]);
+        R.slot0 = slot;
+        R.tile0 = int32_t(slot / TILE);
+        R.ntiles = int32_t((n_rep[r] + TILE - 1) / TILE);
+        R.cell0 = int32_t(cells);
+        R.ncells = int32_t(nc_tot);
+        R.id0 = int32_t(ids);
+        slot += int64_t(R.ntiles) * TILE;
+        cells += nc_tot;
+        ids += n_rep[r];
+        rho_max = std::max(rho_max, double(n_rep[r]) / (R.L[0] * R.L[1] * R.L[2]));
+        if (slot > MAX_SLOTS || cells > (int64_t(1) << 30))
+            return fail(MD_ERR_CELL_OVERFLOW, "more than 2^26 atom slots or 2^30 cells");
+    }
+    P->nslots = slot;
+    P->ntiles = int32_t(slot / TILE);
+    P->ncells = int32_t(cells);
+    P->nchunks = int32_t((cells + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    P->n_total = ids;
+    P->tile_rep.resize(P->ntiles);
+    for (int32_t r = 0; r < nrep; ++r)
+        for (int32_t k = 0; k < P->reps[r].ntiles; ++k) P->tile_rep[P->reps[r].tile0 + k] = r;
+    if (p->nbr_capacity > 0) {
+        P->cap = p->nbr_capacity;
+    } else {
+        const double mean = 4.0 / 3.0 * M_PI * rl * rl * rl * rho_max;
+        P->cap = std::max(8, int(std::ceil(1.5 * mean + 16.0)));
+        P->cap = (P->cap + 3) & ~3;
+    }
+    if (P->cap > 4096) return fail(MD_ERR_INVALID_ARG, "nbr_capacity above 4096");
+    P->series_cap = 1024;
+    return MD_OK;
+}
+
+size_t carve(const Plan& P, char* base, Arrays* A)
+{
+    Carver c{base};
+    Arrays a;
+    std::memset(&a, 0, sizeof(a));
+    const size_t ns = size_t(P.nslots);
+    const bool f64 = P.mode == MD_FP64, f32 = P.mode == MD_FP32;
+    for (int b = 0; b < 2; ++b) {
+        if (f64) a.pos64[b] = c.take<double4_32a>(ns);
+        else a.pos32[b] = c.take<float4>(ns);
+    }
+    for (int q = 0; q < 3; ++q) a.xl[q] = c.take<double>(ns);
+    for (int q = 0; q < 3; ++q) {
+        if (f32) a.v32[q] = c.take<float>(ns);
+        else a.v[q] = c.take<double>(ns);
+    }
+    a.f = c.take<double4_32a>(ns);
+    a.wvir = c.take<double>(ns);
+    a.id = c.take<int32_t>(ns);
+    a.cell = c.take<int32_t>(ns);
+    a.layer = c.take<int32_t>(ns);
+    a.nbr_count = c.take<int32_t>(ns);
+    a.W = c.take<uint32_t>(ns * size_t(P.cap));
+    if (P.rule == MD_REBUILD_DISP) a.xref = c.take<float4>(ns);
+    a.perm = c.take<int32_t>(ns);
+    if (!f32) for (int q = 0; q < 3; ++q) a.tmp_d[q] = c.take<double>(ns);
+    for (int q = 0; q < 3; ++q) a.tmp_v[q] = c.take<double>(ns);
+    for (int q = 0; q < 2; ++q) a.tmp_i[q] = c.take<int32_t>(ns);
+    if (f64) a.tmp_p64 = c.take<double4_32a>(ns);
+    else a.tmp_p32 = c.take<float4>(ns);
+    a.ccount = c.take<int32_t>(size_t(P.ncells));
+    a.cstart = c.take<int32_t>(size_t(P.ncells) + 1);
+    a.chunk = c.take<int32_t>(size_t(P.nchunks));
+    a.tile_rep = c.take<int32_t>(size_t(P.ntiles));
+    a.tile_part = c.take<double>(size_t(P.ntiles) * NPROP);
+    a.rep = c.take<Rep>(size_t(P.nrep));
+    a.rs = c.take<RepState>(size_t(P.nrep));
+    a.props = c.take<md_props>(size_t(P.nrep));
+    a.series = c.take<double>(size_t(P.nrep) * P.series_cap * SERIES_COLS);
+    a.g = c.take<Global>(1);
+    for (int q = 0; q < 3; ++q) a.xchg[q] = c.take<double>(size_t(P.n_total) * 3);
+    if (A) *A = a;
+    return (c.off + 255) & ~size_t(255);
+}
+
+}  // namespace
+
+struct md_system {
+    struct EvPair {
+        cudaEvent_t a, b;
+        int phase;
+    };
+    md_params p;
+    Plan plan;
+    Arrays A;
+    Scal S;
+    Launch L;
+    int cur = 0;
+    int nsm = 0;
+    int64_t host_step = 0;
+    bool binned_fresh = false;
+    md_tuning tune;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // per-phase timers (CUDA events on the system's stream) and kernel-launch counts
+    bool timing = false;
+    std::vector<EvPair> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[MD_NPHASE] = {0};
+    int64_t calls[MD_NPHASE] = {0};
+    int64_t launches[MD_NPHASE] = {0};
+
+    cudaEvent_t take_event()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ~md_system()
+    {
+        for (auto& pr : pending) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+// Brackets one phase of work: counts its kernel launches and, with timing on, records a pair
+// of events around it on the system's stream.
+struct Phase {
+    md_system* s;
+    int ph;
+    cudaEvent_t b = nullptr;
+    Phase(md_system* s_, int ph_, int nlaunch) : s(s_), ph(ph_)
+    {
+        s->launches[ph] += nlaunch;
+        s->calls[ph] += 1;
+        if (s->timing) {
+            cudaEvent_t a = s->take_event();
+            b = s->take_event();
+            cudaEventRecord(a, s->L.stream);
+            s->pending.push_back({a, b, ph});
+        }
+    }
+    ~Phase()
+    {
+        if (b) cudaEventRecord(b, s->L.stream);
+    }
+};
+
+}  // namespace
+
+namespace {
+
+void fill_scal(md_system* s)
+{
+    const md_params& p = s->p;
+    const Plan& P = s->plan;
+    Scal& S = s->S;
+    std::memset(&S, 0, sizeof(S));
+    S.nslots = P.nslots;
+    S.ntiles = P.ntiles;
+    S.nrep = P.nrep;
+    S.ncells = P.ncells;
+    S.nchunks = P.nchunks;
+    S.cap = P.cap;
+    S.mode = P.mode;
+    S.rule = P.rule;
+    S.reorder_every = p.reorder_every;
+    S.series_cap = P.series_cap;
+    S.shift = p.shift_energy;
+    S.dt = p.dt;
+    S.mass = p.mass;
+    S.c = p.dt / (2.0 * p.mass);
+    S.half_skin = 0.5 * p.skin;
+    const double rl = p.rc + p.skin;
+    S.rc2d = p.rc * p.rc;
+    S.rl2d = rl * rl;
+    S.sig2d = p.sigma * p.sigma;
+    S.eps4d = 4.0 * p.eps;
+    S.eps48d = 48.0 * p.eps;
+    double uc = 0.0;
+    if (p.shift_energy) {
+        const double q2 = S.sig2d / S.rc2d, q6 = q2 * q2 * q2;
+        uc = 4.0 * p.eps * (q6 * q6 - q6);
+    }
+    S.ucd = uc;
+    S.rc2f = float(S.rc2d);
+    S.rl2f = float(S.rl2d);
+    S.sig2f = float(S.sig2d);
+    S.eps4f = float(S.eps4d);
+    S.eps48f = float(S.eps48d);
+    S.ucf = float(uc);
+}
+
+int apply_tuning(md_system* s)
+{
+    const int per_sm = std::max(1, s->tune.ctas_per_sm);
+    s->L.grid = std::max(1, s->nsm * per_sm);
+    s->L.step_block = TILE;
+    s->L.build_block = TILE;
+    return MD_OK;
+}
+
+int latch_error(md_system* s)
+{
+    Global g;
+    GBMD_CUDA(cudaMemcpyAsync(&g, s->A.g, sizeof(Global), cudaMemcpyDeviceToHost, s->L.stream));
+    GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    if (g.err == 0) return MD_OK;
+    const int zero = 0;
+    GBMD_CUDA(cudaMemcpyAsync(&s->A.g->err, &zero, sizeof(int), cudaMemcpyHostToDevice, s->L.stream));
+    GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    if (g.err & ERR_NBR_OVERFLOW)
+        return fail(MD_ERR_NBR_OVERFLOW, "neighbour capacity " + std::to_string(s->plan.cap) +
+                                             " exceeded (an atom had " + std::to_string(g.max_nbr_seen) + ")");
+    if (g.err & ERR_NONFINITE) return fail(MD_ERR_NONFINITE, "non-finite velocity or displacement");
+    if (g.err & ERR_TIMEOUT) return fail(MD_ERR_TIMEOUT, "a bounded device wait gave up");
+    return fail(MD_ERR_CUDA, "unknown device error word");
+}
+
+int load_state(md_system* s, const double* x, const double* v)
+{
+    const size_t bytes = size_t(s->plan.n_total) * 3 * sizeof(double);
+    GBMD_CUDA(cudaMemcpyAsync(s->A.xchg[0], x, bytes, cudaMemcpyDefault, s->L.stream));
+    GBMD_CUDA(cudaMemcpyAsync(s->A.xchg[1], v, bytes, cudaMemcpyDefault, s->L.stream));
+    s->cur = 0;
+    GBMD_CUDA(launch_set_state(s->A, s->S, s->L, s->cur));
+    GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, 1));
+    GBMD_CUDA(launch_rebuild(s->A, s->S, s->L, s->cur, true));
+    s->host_step = 0;
+    s->binned_fresh = false;
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* md_last_error(void) { return g_last_error.c_str(); }
+
+size_t md_workspace_bytes_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, const double* box_rep)
+{
+    Plan P;
+    if (make_plan(p, nrep, n_rep, box_rep, &P) != MD_OK) return 0;
+    return carve(P, nullptr, nullptr);
+}
+
+size_t md_workspace_bytes(const md_params* p)
+{
+    if (!p) return 0;
+    const int64_t n = p->n;
+    return md_workspace_bytes_batch(p, 1, &n, p->box);
+}
+
+int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, const double* box_rep,
+                    void* d_workspace, size_t workspace_bytes, const double* x0, const double* v0,
+                    void* stream, md_system** out)
+{
+    if (!out) return fail(MD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!x0 || !v0) return fail(MD_ERR_INVALID_ARG, "x0 and v0 are required");
+    Plan P;
+    int rc = make_plan(p, nrep, n_rep, box_rep, &P);
+    if (rc) return rc;
+    const size_t need = carve(P, nullptr, nullptr);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+        return fail(MD_ERR_WORKSPACE, "workspace missing or not 256-byte aligned");
+    if (workspace_bytes < need)
+        return fail(MD_ERR_WORKSPACE, "workspace has " + std::to_string(workspace_bytes) + " bytes, needs " +
+                                          std::to_string(need));
+    cudaPointerAttributes attr;
+    GBMD_CUDA(cudaPointerGetAttributes(&attr, d_workspace));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(MD_ERR_WORKSPACE, "workspace is not device memory");
+    int dev = 0;
+    GBMD_CUDA(cudaGetDevice(&dev));
+    if (attr.device != dev) return fail(MD_ERR_WORKSPACE, "workspace lives on another device than the current one");
+
+    md_system* s = new (std::nothrow) md_system();
+    if (!s) return fail(MD_ERR_INVALID_ARG, "out of host memory");
+    s->p = *p;
+    s->plan = std::move(P);
+    s->ws = d_workspace;
+    s->ws_bytes = workspace_bytes;
+    carve(s->plan, static_cast<char*>(d_workspace), &s->A);
+    fill_scal(s);
+    s->L.stream = static_cast<cudaStream_t>(stream);
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
+    s->nsm = prop.multiProcessorCount;
+    s->tune.step_block = TILE;
+    s->tune.build_block = TILE;
+    s->tune.ctas_per_sm = 8;
+    s->tune.use_graph = 0;
+    apply_tuning(s);
+
+    auto bail = [&](int code) { delete s; return code; };
+    if (cudaMemsetAsync(d_workspace, 0, need, s->L.stream) != cudaSuccess) return bail(fail(MD_ERR_CUDA, "memset"));
+    if (cudaMemcpyAsync(s->A.rep, s->plan.reps.data(), sizeof(Rep) * s->plan.nrep, cudaMemcpyHostToDevice,
+                        s->L.stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->A.tile_rep, s->plan.tile_rep.data(), sizeof(int32_t) * s->plan.ntiles,
+                        cudaMemcpyHostToDevice, s->L.stream) != cudaSuccess)
+        return bail(fail(MD_ERR_CUDA, "upload of the replica table"));
+    rc = load_state(s, x0, v0);
+    if (rc) return bail(rc);
+    rc = latch_error(s);
+    if (rc) return bail(rc);
+    *out = s;
+    return MD_OK;
+}
+
+int md_create(const md_params* p, void* d_workspace, size_t workspace_bytes, const double* x0, const double* v0,
+              void* stream, md_system** out)
+{
+    if (!p) return fail(MD_ERR_INVALID_ARG, "params is NULL");
+    const int64_t n = p->n;
+    return md_create_batch(p, 1, &n, p->box, d_workspace, workspace_bytes, x0, v0, stream, out);
+}
+
+int md_destroy(md_system* s)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    cudaStreamSynchronize(s->L.stream);
+    delete s;
+    return MD_OK;
+}
+
+int md_bin_cells(md_system* s)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, s->p.reorder_every == 0 ? 1 : 0));
+    GBMD_CUDA(launch_bin_only(s->A, s->S, s->L, s->cur, false));
+    s->binned_fresh = true;
+    return MD_OK;
+}
+
+int md_build_neighbours(md_system* s)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    if (!s->binned_fresh) {
+        GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, 0));
+        GBMD_CUDA(launch_bin_only(s->A, s->S, s->L, s->cur, false));
+    }
+    GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
+    s->binned_fresh = false;
+    return MD_OK;
+}
+
+int md_compute_forces(md_system* s)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    Phase t(s, MD_PHASE_OTHER, 1);
+    GBMD_CUDA(launch_forces(s->A, s->S, s->L, s->cur));
+    return MD_OK;
+}
+
+int md_integrate(md_system* s, int32_t nsteps)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    if (nsteps < 0) return fail(MD_ERR_INVALID_ARG, "nsteps < 0");
+    if (s->binned_fresh) {      // a md_bin_cells without md_build_neighbours: finish the rebuild
+        Phase t(s, MD_PHASE_BUILD, 2);
+        GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
+        s->binned_fresh = false;
+    }
+    for (int32_t k = 0; k < nsteps; ++k) {
+        const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
+        {
+            Phase t(s, MD_PHASE_STEP, props ? 2 : 1);
+            GBMD_CUDA(launch_step(s->A, s->S, s->L, s->cur, props));
+        }
+        s->cur ^= 1;
+        {
+            Phase t(s, MD_PHASE_BIN, 6);
+            GBMD_CUDA(launch_bin_order(s->A, s->S, s->L, s->cur, false));
+        }
+        {
+            Phase t(s, MD_PHASE_REORDER, 2);
+            GBMD_CUDA(launch_reorder(s->A, s->S, s->L, s->cur));
+        }
+        {
+            Phase t(s, MD_PHASE_BUILD, 2);
+            GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
+        }
+        s->host_step += 1;
+    }
+    return MD_OK;
+}
+
+int md_set_timing(md_system* s, int32_t enable)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    s->timing = enable != 0;
+    return MD_OK;
+}
+
+int md_get_timing(md_system* s, double* ms, int64_t* calls, int64_t* launches)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    for (auto& pr : s->pending) {
+        float t = 0.0f;
+        GBMD_CUDA(cudaEventElapsedTime(&t, pr.a, pr.b));
+        s->ms[pr.phase] += double(t);
+        s->pool.push_back(pr.a);
+        s->pool.push_back(pr.b);
+    }
+    s->pending.clear();
+    for (int k = 0; k < MD_NPHASE; ++k) {
+        if (ms) ms[k] = s->ms[k];
+        if (calls) calls[k] = s->calls[k];
+        if (launches) launches[k] = s->launches[k];
+        s->ms[k] = 0.0;
+        s->calls[k] = 0;
+        s->launches[k] = 0;
+    }
+    return MD_OK;
+}
+
+int md_reduce_props(md_system* s, md_props* out)
+{
+    if (!s || !out) return fail(MD_ERR_INVALID_ARG, "system or out is NULL");
+    {
+        Phase t(s, MD_PHASE_PROPS, 3);
+        GBMD_CUDA(launch_props(s->A, s->S, s->L, s->cur, true, false));
+    }
+    GBMD_CUDA(cudaMemcpyAsync(out, s->A.props, sizeof(md_props) * s->plan.nrep, cudaMemcpyDeviceToHost,
+                              s->L.stream));
+    return latch_error(s);
+}
+
+int md_get_series(md_system* s, double* out, int32_t max_rows, int32_t* rows)
+{
+    if (!s || !out || !rows || max_rows < 0) return fail(MD_ERR_INVALID_ARG, "bad arguments");
+    std::vector<RepState> st(s->plan.nrep);
+    GBMD_CUDA(cudaMemcpyAsync(st.data(), s->A.rs, sizeof(RepState) * st.size(), cudaMemcpyDeviceToHost,
+                              s->L.stream));
+    GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    int32_t nr = 0;
+    for (auto& x : st) nr = std::max(nr, x.series_rows);
+    nr = std::min(nr, max_rows);
+    for (int32_t r = 0; r < s->plan.nrep; ++r) {
+        GBMD_CUDA(cudaMemcpyAsync(out + size_t(r) * max_rows * SERIES_COLS,
+                                  s->A.series + size_t(r) * s->plan.series_cap * SERIES_COLS,
+                                  sizeof(double) * SERIES_COLS * nr, cudaMemcpyDeviceToHost, s->L.stream));
+    }
+    *rows = nr;
+    return latch_error(s);
+}
+
+int md_clear_series(md_system* s)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    std::vector<RepState> st(s->plan.nrep);
+    GBMD_CUDA(cudaMemcpyAsync(st.data(), s->A.rs, sizeof(RepState) * st.size(), cudaMemcpyDeviceToHost,
+                              s->L.stream));
+    GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    for (auto& x : st) x.series_rows = 0;
+    GBMD_CUDA(cudaMemcpyAsync(s->A.rs, st.data(), sizeof(RepState) * st.size(), cudaMemcpyHostToDevice,
+                              s->L.stream));
+    GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    return MD_OK;
+}
+
+int md_get_state(md_system* s, double* x, double* v, double* f)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    if (!x && !v && !f) return MD_OK;
+    {
+        Phase t(s, MD_PHASE_OTHER, (v || f) ? 2 : 1);
+        if (v || f) GBMD_CUDA(launch_forces(s->A, s->S, s->L, s->cur));
+        GBMD_CUDA(launch_get_state(s->A, s->S, s->L, s->cur, v != nullptr, f != nullptr));
+    }
+    const size_t bytes = size_t(s->plan.n_total) * 3 * sizeof(double);
+    if (x) GBMD_CUDA(cudaMemcpyAsync(x, s->A.xchg[0], bytes, cudaMemcpyDefault, s->L.stream));
+    if (v) GBMD_CUDA(cudaMemcpyAsync(v, s->A.xchg[1], bytes, cudaMemcpyDefault, s->L.stream));
+    if (f) GBMD_CUDA(cudaMemcpyAsync(f, s->A.xchg[2], bytes, cudaMemcpyDefault, s->L.stream));
+    return latch_error(s);
+}
+
+int md_set_state(md_system* s, const double* x, const double* v)
+{
+    if (!s || !x || !v) return fail(MD_ERR_INVALID_ARG, "system, x and v are required");
+    int rc = load_state(s, x, v);
+    if (rc) return rc;
+    return latch_error(s);
+}
+
+int md_get_cells(md_system* s, int32_t* cell)
+{
+    if (!s || !cell) return fail(MD_ERR_INVALID_ARG, "system or cell is NULL");
+    int32_t* tmp = reinterpret_cast<int32_t*>(s->A.xchg[0]);
+    GBMD_CUDA(launch_get_cells(s->A, s->S, s->L, tmp));
+    GBMD_CUDA(cudaMemcpyAsync(cell, tmp, sizeof(int32_t) * s->plan.n_total, cudaMemcpyDefault, s->L.stream));
+    return latch_error(s);
+}
+
+int md_get_neighbours(md_system* s, int32_t* counts, int32_t* nbr_ids, int32_t cap)
+{
+    if (!s || !counts || !nbr_ids || cap <= 0) return fail(MD_ERR_INVALID_ARG, "bad arguments");
+    // counts staged in xchg[0]; rows staged in xchg[1] (6 int32 per atom) one id window at a time
+    const int64_t n = s->plan.n_total;
+    int32_t* dcounts = reinterpret_cast<int32_t*>(s->A.xchg[0]);
+    int32_t* drows = reinterpret_cast<int32_t*>(s->A.xchg[1]);
+    const int64_t window = std::max<int64_t>(1, (n * 6) / cap);
+    for (int64_t lo = 0; lo < n; lo += window) {
+        const int64_t hi = std::min(n, lo + window);
+        GBMD_CUDA(launch_get_neighbours(s->A, s->S, s->L, dcounts, drows, cap, lo, hi));
+        GBMD_CUDA(cudaMemcpyAsync(nbr_ids + lo * cap, drows, sizeof(int32_t) * (hi - lo) * cap, cudaMemcpyDefault,
+                                  s->L.stream));
+    }
+    GBMD_CUDA(cudaMemcpyAsync(counts, dcounts, sizeof(int32_t) * n, cudaMemcpyDefault, s->L.stream));
+    return latch_error(s);
+}
+
+int md_check(md_system* s)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    GBMD_CUDA(cudaGetLastError());
+    return latch_error(s);
+}
+
+int32_t md_nrep(const md_system* s) { return s ? s->plan.nrep : 0; }
+int64_t md_natoms(const md_system* s) { return s ? s->plan.n_total : 0; }
+int32_t md_nbr_capacity(const md_system* s) { return s ? s->plan.cap : 0; }
+
+int md_cells_per_axis(const md_system* s, int32_t r, int32_t* nc)
+{
+    if (!s || !nc || r < 0 || r >= s->plan.nrep) return fail(MD_ERR_INVALID_ARG, "bad arguments");
+    for (int a = 0; a < 3; ++a) nc[a] = s->plan.reps[r].nc[a];
+    return MD_OK;
+}
+
+int md_set_tuning(md_system* s, const md_tuning* t)
+{
+    if (!s || !t) return fail(MD_ERR_INVALID_ARG, "bad arguments");
+    if (t->step_block && t->step_block != TILE) return fail(MD_ERR_INVALID_ARG, "step_block must be 128");
+    if (t->build_block && t->build_block != TILE) return fail(MD_ERR_INVALID_ARG, "build_block must be 128");
+    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(MD_ERR_INVALID_ARG, "ctas_per_sm in 0..64");
+    if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
+    s->tune.use_graph = t->use_graph;
+    return apply_tuning(s);
+}
+
+int md_get_tuning(const md_system* s, md_tuning* t)
+{
+    if (!s || !t) return fail(MD_ERR_INVALID_ARG, "bad arguments");
+    *t = s->tune;
+    return MD_OK;
+}
+
+}  // extern "C"

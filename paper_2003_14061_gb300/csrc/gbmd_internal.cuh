@@ -1,0 +1,213 @@
+// gbmd_internal.cuh -- device data layout and helpers shared by the kernels of libgbmd.so.
+//
+// Layout in HBM (all arrays carved from the caller's workspace):
+//   * Atoms live in "slots".  Replica r owns slots [slot0_r, slot0_r + n_r); slot0_r is a
+//     multiple of TILE, so every tile of TILE slots belongs to exactly one replica and the tail
+//     of a replica's last tile is padding.  One tile is the work unit of one CTA iteration.
+//   * Positions used by the pair loops are cell-local: pos = (x - origin(cell), packed cell),
+//     float4 for MD_MIXED/MD_FP32 and double4_32a for MD_FP64, double-buffered (read A, write B).
+//     The cell coordinates (c_x, c_y, c_z) are packed as c_x | c_y << 10 | c_z << 20 in .w.
+//     Cell-local coordinates keep FP32 pair distances at ~1e-7 absolute in any box size.
+//   * MD_MIXED/MD_FP64 keep the master state in FP64 SoA streams: xl[3] (cell-local position)
+//     and v[3].  MD_FP32 keeps pos (float4) and v32[3] as its master state.
+//   * The neighbour matrix W is row-major, W[m * nslots + slot] (Sec. 2.3: the m-th neighbours of
+//     consecutive atoms are adjacent, so the per-atom loop reads it coalesced).  An entry holds
+//     the neighbour slot in bits 0..25 and (o_x+1) | (o_y+1) << 2 | (o_z+1) << 4 in bits 26..31,
+//     o being the periodic offset of the neighbour's cell relative to the atom's cell.
+//   * Cells are numbered globally: replica r's cells are cell0_r + (c_z n_y + c_y) n_x + c_x.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbmd.h"
+
+namespace gbmd {
+
+constexpr int TILE = 128;                 // slots per tile
+constexpr int NPROP = 8;                  // U, K, W, px, py, pz, (spare), vmax^2
+constexpr int SERIES_COLS = 9;            // step, U, K, W, P, px, py, pz, vmax
+constexpr uint32_t IDX_MASK = 0x03FFFFFFu;
+constexpr int64_t MAX_SLOTS = int64_t(1) << 26;
+constexpr int MAX_NC = 1023;
+constexpr int SCAN_CHUNK = 2048;          // cells per block of the prefix sum
+
+enum ErrBits { ERR_NBR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
+
+struct Rep {                  // per replica, fixed after creation
+    int64_t slot0;            // first slot
+    int32_t n;                // atoms
+    int32_t tile0;            // first tile
+    int32_t ntiles;
+    int32_t cell0;            // first global cell id
+    int32_t ncells;
+    int32_t id0;              // first permanent id
+    int32_t nc[3];            // cells per axis
+    int32_t pad;
+    double L[3];              // box sides
+    double w[3];              // cell sides L / n_c
+    double s[3];              // n_c / L
+    float wf[3];              // (float) w
+    float pad2;
+};
+
+struct RepState {             // per replica, mutable on the device
+    double D;                 // accumulated displacement bound (rule VMAX)
+    unsigned int vmax2;       // max |v|^2 or |dx|^2 of this step, as float bits
+    int32_t rebuild;          // 1: rebuild before the next force evaluation
+    int32_t reorder;          // 1: the pending rebuild reorders too
+    int32_t vhalf;            // 1: v holds v_{n-1/2}; 0: v holds v_n
+    int32_t tiles_done;       // last-tile-done counter of the step kernel
+    int32_t max_nbrs;         // max m_i at the last rebuild
+    int32_t max_occ;          // max k_c at the last rebuild
+    int32_t series_rows;      // rows written to the time series
+    int64_t step;
+    int64_t rebuilds;
+    int64_t last_reorder;     // step of the last reorder
+    int64_t sum_nbrs;         // sum m_i at the last rebuild
+};
+
+struct Global {               // device-wide words
+    int32_t any_rebuild;      // some replica needs a rebuild before the next force pass
+    int32_t any_reorder;      // some rebuilding replica reorders
+    int32_t err;              // ErrBits, latched
+    int32_t max_nbr_seen;     // largest m_i that overflowed
+};
+
+struct Arrays {
+    // per slot
+    float4* pos32[2];
+    double4_32a* pos64[2];
+    double* xl[3];
+    double* v[3];
+    float* v32[3];
+    double4_32a* f;               // forces and u_i (md_compute_forces)
+    double* wvir;             // per-atom virial sum_j r_ij . f_ij (md_compute_forces)
+    int32_t* id;
+    int32_t* cell;
+    int32_t* layer;
+    int32_t* nbr_count;
+    uint32_t* W;
+    float4* xref;             // positions at the last rebuild (rule DISP)
+    int32_t* perm;            // cell-ordered slots (the matrix H of Sec. 2.3, flattened)
+    // reorder scratch, per slot
+    double* tmp_d[3];
+    double* tmp_v[3];
+    int32_t* tmp_i[2];
+    float4* tmp_p32;
+    double4_32a* tmp_p64;
+    // per cell
+    int32_t* ccount;
+    int32_t* cstart;
+    int32_t* chunk;           // per SCAN_CHUNK cells
+    // per tile
+    int32_t* tile_rep;
+    double* tile_part;        // NPROP per tile
+    // per replica
+    Rep* rep;
+    RepState* rs;
+    md_props* props;          // per replica, output of the props reduction
+    double* series;           // [nrep][series_cap][SERIES_COLS]
+    Global* g;
+    // id-ordered exchange buffers (3 doubles per atom)
+    double* xchg[3];
+};
+
+struct Scal {
+    int64_t nslots;
+    int32_t ntiles;
+    int32_t nrep;
+    int32_t ncells;
+    int32_t nchunks;
+    int32_t cap;              // rows of W
+    int32_t mode;             // md_precision
+    int32_t rule;             // md_rebuild_rule
+    int32_t reorder_every;
+    int32_t series_cap;
+    int32_t shift;
+    double dt, mass, c;       // c = dt / (2 m)
+    double half_skin;
+    double rc2d, rl2d, sig2d, eps4d, eps48d, ucd;
+    float rc2f, rl2f, sig2f, eps4f, eps48f, ucf;
+};
+
+// ------------------------------------------------------------------------------------------
+// small device helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz)
+{
+    return uint32_t(cx) | (uint32_t(cy) << 10) | (uint32_t(cz) << 20);
+}
+
+__device__ __forceinline__ void unpack_cell(uint32_t p, int& cx, int& cy, int& cz)
+{
+    cx = int(p & 1023u);
+    cy = int((p >> 10) & 1023u);
+    cz = int((p >> 20) & 1023u);
+}
+
+__device__ __forceinline__ uint32_t cell_bits(float w) { return __float_as_uint(w); }
+__device__ __forceinline__ uint32_t cell_bits(double w) { return uint32_t(__double2uint_rz(w)); }
+__device__ __forceinline__ float cell_word_f(uint32_t p) { return __uint_as_float(p); }
+__device__ __forceinline__ double cell_word_d(uint32_t p) { return double(p); }
+
+// Warp-wide sums and maxima.
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ float warp_max(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ int warp_max_i(int x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launch wrappers (defined in the .cu files)
+// ------------------------------------------------------------------------------------------
+struct Launch {
+    cudaStream_t stream;
+    int grid;                 // persistent CTAs for tile loops
+    int step_block;
+    int build_block;
+};
+
+// rebuild path (kernels_rebuild.cu)
+cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder);
+cudaError_t launch_rebuild(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
+cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
+cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);   // 6 kernels
+cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur);                    // 2 kernels
+cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur);                // 2 kernels
+
+// step path (kernels_step.cu)
+cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props);
+cudaError_t launch_forces(const Arrays& A, const Scal& S, const Launch& L, int cur);
+cudaError_t launch_props(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_forces,
+                         bool to_series);
+cudaError_t launch_get_state(const Arrays& A, const Scal& S, const Launch& L, int cur, bool want_v,
+                             bool want_f);
+cudaError_t launch_set_state(const Arrays& A, const Scal& S, const Launch& L, int cur);
+cudaError_t launch_get_cells(const Arrays& A, const Scal& S, const Launch& L, int32_t* out_by_id);
+cudaError_t launch_get_neighbours(const Arrays& A, const Scal& S, const Launch& L, int32_t* counts_by_id,
+                                  int32_t* nbr_by_id, int32_t cap_out, int64_t id_lo, int64_t id_hi);
+
+}  // namespace gbmd

@@ -1,0 +1,474 @@
+// kernels_rebuild.cu -- cell binning, cell ordering, reordering and neighbour-matrix build.
+//
+// Sec. 2.3 of the paper lists the steps N1-N5; Sec. 2.4 item 4 the reorder vector s obtained
+// there by a serial host pass over H and, as the GPU alternative it names, by a prefix sum of
+// the cell occupancies k_c.  Here everything runs on the GPU:
+//   k_bin          N1 + N2: cell of every atom from its FP64 position, layer l_i = atomic slot
+//                  in the cell (the occupancy counter k_c); max k_c (N3) per replica.
+//   k_scan_*       prefix sum of k_c -> cstart (the row offsets of H, Sec. 2.4 item 4).
+//   k_scatter      N4: H flattened: perm[cstart[c] + l_i] = i.
+//   k_sort_cells   the atomic layer order is indeterminate (Sec. 2.3 notes the resulting
+//                  irreproducibility); sorting each cell's slots makes the order, and every
+//                  result after it, deterministic.
+//   k_reorder_*    Sec. 4.1 item 1: permute the atoms into cell order (gather through scratch).
+//   k_build        N5: W from the 27 neighbouring cells; W stored row-major for coalescing
+//                  (Sec. 4.1 item 6).
+// Only replicas whose rebuild flag is set do work; kernels return at once when none is set, so
+// the whole sequence can sit in every step of md_integrate.
+#include <algorithm>
+
+#include "gbmd_internal.cuh"
+
+namespace gbmd {
+
+// ------------------------------------------------------------------------------------------
+// N1 + N2
+// ------------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int from_set)
+{
+    if (!A.g->any_rebuild) return;
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const int r = A.tile_rep[t];
+        if (!A.rs[r].rebuild) continue;
+        const Rep& R = A.rep[r];
+        if (t == R.tile0 && threadIdx.x == 0) {
+            A.rs[r].sum_nbrs = 0;
+            A.rs[r].max_nbrs = 0;
+        }
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const int64_t j = slot - R.slot0;
+        int occ = 0;
+        if (j < R.n) {
+            double x[3];
+            uint32_t pw;
+            if (from_set) {            // md_set_state left global positions in xl, origin (0,0,0)
+                x[0] = A.xl[0][slot]; x[1] = A.xl[1][slot]; x[2] = A.xl[2][slot];
+                pw = 0u;
+            } else if (MODE == MD_FP32) {
+                const float4 p = A.pos32[cur][slot];
+                x[0] = p.x; x[1] = p.y; x[2] = p.z;
+                pw = __float_as_uint(p.w);
+            } else {
+                x[0] = A.xl[0][slot]; x[1] = A.xl[1][slot]; x[2] = A.xl[2][slot];
+                pw = (MODE == MD_FP64) ? cell_bits(A.pos64[cur][slot].w)
+                                       : __float_as_uint(A.pos32[cur][slot].w);
+            }
+            int oc[3];
+            unpack_cell(pw, oc[0], oc[1], oc[2]);
+            int c[3];
+            double loc[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // global coordinate, wrapped once into [0, L)
+                double xa = __dadd_rn(__dmul_rn(double(oc[a]), R.w[a]), x[a]);
+                if (xa < 0.0) xa = __dadd_rn(xa, R.L[a]);
+                if (xa >= R.L[a]) xa = __dsub_rn(xa, R.L[a]);
+                int ca = int(floor(__dmul_rn(xa, R.s[a])));
+                ca = min(max(ca, 0), R.nc[a] - 1);
+                c[a] = ca;
+                loc[a] = __dsub_rn(xa, __dmul_rn(double(ca), R.w[a]));
+            }
+            const uint32_t packed = pack_cell(c[0], c[1], c[2]);
+            if (MODE == MD_FP64) {
+                A.pos64[cur][slot] = make_double4_32a(loc[0], loc[1], loc[2], cell_word_d(packed));
+            } else {
+                A.pos32[cur][slot] = make_float4(__double2float_rn(loc[0]), __double2float_rn(loc[1]),
+                                                 __double2float_rn(loc[2]), cell_word_f(packed));
+            }
+            if (MODE != MD_FP32) {
+                A.xl[0][slot] = loc[0]; A.xl[1][slot] = loc[1]; A.xl[2][slot] = loc[2];
+            }
+            const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+            A.cell[slot] = cell;
+            const int l = atomicAdd(&A.ccount[cell], 1);
+            A.layer[slot] = l;
+            occ = l + 1;
+        }
+        occ = warp_max_i(occ);
+        if ((threadIdx.x & 31) == 0 && occ > 0) atomicMax(&A.rs[r].max_occ, occ);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// prefix sum of the cell occupancies (three passes, no inter-block waiting)
+// ------------------------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_PER_THREAD = SCAN_CHUNK / SCAN_THREADS;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < (blockDim.x >> 5)) ? sh_warp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < (blockDim.x >> 5)) sh_warp[lane] = wi - w;
+        if (lane == (blockDim.x >> 5) - 1) sh_warp[32] = wi;
+    }
+    __syncthreads();
+    total = sh_warp[32];
+    const int r = sh_warp[wid] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    __shared__ int sh[33];
+    const int64_t base = int64_t(blockIdx.x) * SCAN_CHUNK + threadIdx.x * SCAN_PER_THREAD;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        const int64_t c = base + k;
+        if (c < S.ncells) s += A.ccount[c];
+    }
+    int total;
+    block_exclusive_scan(s, sh, total);
+    if (threadIdx.x == 0) A.chunk[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    __shared__ int sh[33];
+    int carry = 0;
+    for (int b0 = 0; b0 < S.nchunks; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const int v = (b < S.nchunks) ? A.chunk[b] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, sh, total);
+        if (b < S.nchunks) A.chunk[b] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    __shared__ int sh[33];
+    const int64_t base = int64_t(blockIdx.x) * SCAN_CHUNK + threadIdx.x * SCAN_PER_THREAD;
+    int v[SCAN_PER_THREAD];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        const int64_t c = base + k;
+        v[k] = (c < S.ncells) ? A.ccount[c] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = A.chunk[blockIdx.x] + block_exclusive_scan(s, sh, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+        const int64_t c = base + k;
+        if (c < S.ncells) {
+            A.cstart[c] = run;
+            A.ccount[c] = 0;              // ready for the next binning
+            run += v[k];
+            if (c == S.ncells - 1) A.cstart[S.ncells] = run;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// N4 and the deterministic order within cells
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) k_scatter(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const int r = A.tile_rep[t];
+        if (!A.rs[r].rebuild) continue;
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        if (slot - R.slot0 < R.n) A.perm[A.cstart[A.cell[slot]] + A.layer[slot]] = int32_t(slot);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sort_cells(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < S.ncells;
+         c += int64_t(gridDim.x) * blockDim.x) {
+        const int b = A.cstart[c], e = A.cstart[c + 1];
+        for (int k = b + 1; k < e; ++k) {            // insertion sort, cells hold a few atoms
+            const int32_t key = A.perm[k];
+            int q = k - 1;
+            while (q >= b && A.perm[q] > key) {
+                A.perm[q + 1] = A.perm[q];
+                --q;
+            }
+            A.perm[q + 1] = key;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// reorder (Sec. 4.1 item 1): new slot slot0 + j takes the j-th atom in cell order
+// ------------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(TILE) k_reorder_gather(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_reorder) return;
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const int r = A.tile_rep[t];
+        if (!(A.rs[r].rebuild && A.rs[r].reorder)) continue;
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const int64_t j = slot - R.slot0;
+        if (j >= R.n) continue;
+        const int32_t src = A.perm[A.cstart[R.cell0] + j];
+        if (MODE == MD_FP32) {
+            A.tmp_p32[slot] = A.pos32[cur][src];
+            for (int a = 0; a < 3; ++a) A.tmp_v[a][slot] = double(A.v32[a][src]);
+        } else {
+            if (MODE == MD_FP64) A.tmp_p64[slot] = A.pos64[cur][src];
+            else A.tmp_p32[slot] = A.pos32[cur][src];
+            for (int a = 0; a < 3; ++a) {
+                A.tmp_d[a][slot] = A.xl[a][src];
+                A.tmp_v[a][slot] = A.v[a][src];
+            }
+        }
+        A.tmp_i[0][slot] = A.id[src];
+        A.tmp_i[1][slot] = A.cell[src];
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TILE) k_reorder_copy(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_reorder) return;
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const int r = A.tile_rep[t];
+        if (!(A.rs[r].rebuild && A.rs[r].reorder)) continue;
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const int64_t j = slot - R.slot0;
+        if (j >= R.n) continue;
+        if (MODE == MD_FP32) {
+            A.pos32[cur][slot] = A.tmp_p32[slot];
+            for (int a = 0; a < 3; ++a) A.v32[a][slot] = float(A.tmp_v[a][slot]);
+        } else {
+            if (MODE == MD_FP64) A.pos64[cur][slot] = A.tmp_p64[slot];
+            else A.pos32[cur][slot] = A.tmp_p32[slot];
+            for (int a = 0; a < 3; ++a) {
+                A.xl[a][slot] = A.tmp_d[a][slot];
+                A.v[a][slot] = A.tmp_v[a][slot];
+            }
+        }
+        A.id[slot] = A.tmp_i[0][slot];
+        A.cell[slot] = A.tmp_i[1][slot];
+        A.perm[A.cstart[R.cell0] + j] = int32_t(slot);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// N5: neighbour matrix.  Criterion (exact, shared with nothing): with lf the cell-local
+// coordinates and o the periodic cell offset, d = (lf_j - lf_i) + o * wf (two roundings),
+// r2 = fma(d_z, d_z, fma(d_y, d_y, d_x * d_x)), neighbour iff r2 < (r_c + skin)^2.
+// ------------------------------------------------------------------------------------------
+template <typename T> struct PosT;
+template <> struct PosT<float> { using type = float4; };
+template <> struct PosT<double> { using type = double4_32a; };
+
+__device__ __forceinline__ uint32_t word_of(const float4& p) { return __float_as_uint(p.w); }
+__device__ __forceinline__ uint32_t word_of(const double4_32a& p) { return cell_bits(p.w); }
+
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T>
+__global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
+{
+    using P4 = typename PosT<T>::type;
+    if (!A.g->any_rebuild) return;
+    const P4* __restrict__ pos = nullptr;
+    if constexpr (sizeof(T) == 8) pos = reinterpret_cast<const P4*>(A.pos64[cur]);
+    else pos = reinterpret_cast<const P4*>(A.pos32[cur]);
+    const T rl2 = (sizeof(T) == 8) ? T(S.rl2d) : T(S.rl2f);
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const int r = A.tile_rep[t];
+        if (!A.rs[r].rebuild) continue;
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const bool active = slot - R.slot0 < R.n;
+        int m = 0;
+        if (active) {
+            const P4 pi = pos[slot];
+            int cx, cy, cz;
+            unpack_cell(word_of(pi), cx, cy, cz);
+            T w[3];
+            if constexpr (sizeof(T) == 8) { w[0] = R.w[0]; w[1] = R.w[1]; w[2] = R.w[2]; }
+            else { w[0] = R.wf[0]; w[1] = R.wf[1]; w[2] = R.wf[2]; }
+            for (int oz = -1; oz <= 1; ++oz) {
+                int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
+                const T offz = T(oz) * w[2];
+                for (int oy = -1; oy <= 1; ++oy) {
+                    int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
+                    const T offy = T(oy) * w[1];
+                    for (int ox = -1; ox <= 1; ++ox) {
+                        int nx = cx + ox; nx += (nx < 0) ? R.nc[0] : 0; nx -= (nx >= R.nc[0]) ? R.nc[0] : 0;
+                        const T offx = T(ox) * w[0];
+                        const int gc = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0] + nx;
+                        const uint32_t code = (uint32_t(ox + 1) | (uint32_t(oy + 1) << 2) |
+                                               (uint32_t(oz + 1) << 4)) << 26;
+                        const int kb = A.cstart[gc], ke = A.cstart[gc + 1];
+                        for (int k = kb; k < ke; ++k) {
+                            const int32_t jslot = A.perm[k];
+                            if (jslot == slot) continue;
+                            const P4 pj = pos[jslot];
+                            const T dx = add_rn(sub_rn(pj.x, pi.x), offx);
+                            const T dy = add_rn(sub_rn(pj.y, pi.y), offy);
+                            const T dz = add_rn(sub_rn(pj.z, pi.z), offz);
+                            const T r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                            if (r2 < rl2) {
+                                if (m < S.cap) A.W[int64_t(m) * S.nslots + slot] = uint32_t(jslot) | code;
+                                ++m;
+                            }
+                        }
+                    }
+                }
+            }
+            A.nbr_count[slot] = m;
+            if (S.rule == MD_REBUILD_DISP) {
+                A.xref[slot] = make_float4(float(pi.x), float(pi.y), float(pi.z), 0.0f);
+            }
+            if (m > S.cap) {
+                atomicOr(&A.g->err, ERR_NBR_OVERFLOW);
+                atomicMax(&A.g->max_nbr_seen, m);
+            }
+        }
+        const long long sum = warp_sum_ll(active ? m : 0);
+        const int mx = warp_max_i(m);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.rs[r].sum_nbrs),
+                      static_cast<unsigned long long>(sum));
+            atomicMax(&A.rs[r].max_nbrs, mx);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// bookkeeping after a rebuild
+// ------------------------------------------------------------------------------------------
+__global__ void k_rebuild_finish(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    for (int r = threadIdx.x; r < S.nrep; r += blockDim.x) {
+        RepState& st = A.rs[r];
+        if (!st.rebuild) continue;
+        if (st.reorder) st.last_reorder = st.step;
+        st.reorder = 0;
+        st.rebuild = 0;
+        st.D = 0.0;
+        st.rebuilds += 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        A.g->any_rebuild = 0;
+        A.g->any_reorder = 0;
+    }
+}
+
+// Mark every replica for a rebuild (creation, md_set_state, md_bin_cells).
+__global__ void k_force_rebuild(Arrays A, Scal S, int reorder)
+{
+    for (int r = threadIdx.x; r < S.nrep; r += blockDim.x) {
+        A.rs[r].rebuild = 1;
+        A.rs[r].reorder = reorder;
+        A.rs[r].max_occ = 0;
+    }
+    if (threadIdx.x == 0) {
+        A.g->any_rebuild = 1;
+        A.g->any_reorder = reorder;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------------
+static int tile_grid(const Scal& S, const Launch& L)
+{
+    return std::max(1, std::min(L.grid, S.ntiles));
+}
+
+cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder)
+{
+    k_force_rebuild<<<1, 256, 0, L.stream>>>(A, S, reorder);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set)
+{
+    const int g = tile_grid(S, L);
+    if (S.mode == MD_FP64) k_bin<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
+    else if (S.mode == MD_MIXED) k_bin<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
+    else k_bin<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
+    k_scan_chunks<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
+    k_scan_top<<<1, 1024, 0, L.stream>>>(A, S);
+    k_scan_apply<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
+    k_scatter<<<g, TILE, 0, L.stream>>>(A, S);
+    const int gs = int(std::min<int64_t>((S.ncells + 255) / 256, int64_t(L.grid) * 8));
+    k_sort_cells<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur)
+{
+    const int g = tile_grid(S, L);
+    if (S.mode == MD_FP64) {
+        k_reorder_gather<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
+        k_reorder_copy<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    } else if (S.mode == MD_MIXED) {
+        k_reorder_gather<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);
+        k_reorder_copy<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    } else {
+        k_reorder_gather<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur);
+        k_reorder_copy<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set)
+{
+    cudaError_t e = launch_bin_order(A, S, L, cur, from_set);
+    if (e != cudaSuccess) return e;
+    return launch_reorder(A, S, L, cur);
+}
+
+cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur)
+{
+    const int g = tile_grid(S, L);
+    if (S.mode == MD_FP64) k_build<double><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else k_build<float><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set)
+{
+    cudaError_t e = launch_bin_only(A, S, L, cur, from_set);
+    if (e != cudaSuccess) return e;
+    return launch_build_only(A, S, L, cur);
+}
+
+}  // namespace gbmd

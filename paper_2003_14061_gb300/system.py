@@ -1,0 +1,207 @@
+"""MDSystem: the C ABI of libgbmd.so with a torch-owned device workspace.
+
+PyTorch provides the device memory (one uint8 tensor) and the stream; every computation is a
+call into the library.  Host arrays are numpy float64; device tensors may be passed instead for
+the initial state and for state exchange (their data pointers go straight to the ABI).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+_PREC = {"fp64": B.MD_FP64, "mixed": B.MD_MIXED, "fp32": B.MD_FP32}
+_RULE = {"vmax": B.MD_REBUILD_VMAX, "disp": B.MD_REBUILD_DISP, "every": B.MD_REBUILD_EVERY}
+WCA_RC = 2.0 ** (1.0 / 6.0)
+
+
+def make_params(*, eps=1.0, sigma=1.0, mass=1.0, rc=WCA_RC, skin=0.4, dt=0.005, shift=True,
+                precision="mixed", reorder_every=100, nbr_capacity=0, rebuild_rule="vmax",
+                props_every=0, n=0, box=(1.0, 1.0, 1.0)) -> B.md_params:
+    p = B.md_params()
+    p.n = int(n)
+    for a in range(3):
+        p.box[a] = float(box[a])
+    p.eps, p.sigma, p.mass, p.rc, p.skin, p.dt = map(float, (eps, sigma, mass, rc, skin, dt))
+    p.shift_energy = int(bool(shift))
+    p.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    p.reorder_every = int(reorder_every)
+    p.nbr_capacity = int(nbr_capacity)
+    p.rebuild_rule = _RULE[rebuild_rule] if isinstance(rebuild_rule, str) else int(rebuild_rule)
+    p.props_every = int(props_every)
+    return p
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a float64 [n,3] numpy array or a contiguous torch tensor."""
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            a = a.to(torch.float64).contiguous()
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr
+
+
+class MDSystem:
+    """One system (``box`` given) or a batch of independent replicas (``n_rep`` and ``boxes``)."""
+
+    def __init__(self, x0, v0, box=None, *, n_rep=None, boxes=None, device=None, stream=None, **kw):
+        self.lib = B.lib()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if n_rep is None:
+            n = int(np.asarray(x0.shape[0]))
+            self.n_rep = np.array([n], dtype=np.int64)
+            self.boxes = np.asarray(box, dtype=np.float64).reshape(1, 3).copy()
+        else:
+            self.n_rep = np.ascontiguousarray(n_rep, dtype=np.int64)
+            self.boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        self.n = int(self.n_rep.sum())
+        self.params = make_params(n=self.n_rep[0], box=self.boxes[0], **kw)
+        nrep = len(self.n_rep)
+        nbytes = self.lib.md_workspace_bytes_batch(ctypes.byref(self.params), nrep,
+                                                   self.n_rep.ctypes.data_as(ctypes.c_void_p),
+                                                   self.boxes.ctypes.data_as(ctypes.c_void_p))
+        if nbytes == 0:
+            raise B.MDError(-1, "md_workspace_bytes_batch", B.last_error())
+        self.workspace_bytes = int(nbytes)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        xp, xk = _ptr(x0)
+        vp, vk = _ptr(v0)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            B.check(self.lib.md_create_batch(ctypes.byref(self.params), nrep,
+                                             self.n_rep.ctypes.data_as(ctypes.c_void_p),
+                                             self.boxes.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.c_void_p(self.workspace.data_ptr()),
+                                             self.workspace_bytes, xp, vp,
+                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle)),
+                    "md_create_batch")
+        self.h = handle
+        del xk, vk
+
+    # -- lifecycle ---------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the hot path ------------------------------------------------------------------------
+    def _call(self, name, *args):
+        with torch.cuda.device(self.device):
+            return B.call(name, self.h, *args)
+
+    def bin_cells(self):
+        self._call("md_bin_cells")
+
+    def build_neighbours(self):
+        self._call("md_build_neighbours")
+
+    def compute_forces(self):
+        self._call("md_compute_forces")
+
+    def integrate(self, nsteps: int):
+        self._call("md_integrate", int(nsteps))
+
+    # -- results -----------------------------------------------------------------------------
+    @property
+    def nrep(self) -> int:
+        return int(self.lib.md_nrep(self.h))
+
+    @property
+    def nbr_capacity(self) -> int:
+        return int(self.lib.md_nbr_capacity(self.h))
+
+    def cells_per_axis(self, r: int = 0):
+        nc = np.zeros(3, dtype=np.int32)
+        self._call("md_cells_per_axis", int(r), nc.ctypes.data_as(ctypes.c_void_p))
+        return nc
+
+    def props(self):
+        out = (B.md_props * self.nrep)()
+        self._call("md_reduce_props", ctypes.cast(out, ctypes.c_void_p))
+        return [o.as_dict() for o in out]
+
+    def series(self, max_rows: int = 1024):
+        buf = np.zeros((self.nrep, max_rows, B.SERIES_COLS))
+        rows = ctypes.c_int32()
+        self._call("md_get_series", buf.ctypes.data_as(ctypes.c_void_p), int(max_rows), ctypes.byref(rows))
+        return buf[:, : rows.value]
+
+    def clear_series(self):
+        self._call("md_clear_series")
+
+    def state(self, x=True, v=True, f=False):
+        """(x, v, f) in id order as numpy [n,3] float64 (None where not requested)."""
+        out = [np.zeros((self.n, 3)) if w else None for w in (x, v, f)]
+        ptrs = [o.ctypes.data_as(ctypes.c_void_p) if o is not None else None for o in out]
+        self._call("md_get_state", *ptrs)
+        return tuple(out)
+
+    def state_into(self, x: torch.Tensor = None, v: torch.Tensor = None, f: torch.Tensor = None):
+        """Write the state into device (or pinned host) float64 tensors of shape [n,3]."""
+        ptrs = [ctypes.c_void_p(t.data_ptr()) if t is not None else None for t in (x, v, f)]
+        self._call("md_get_state", *ptrs)
+
+    def set_state(self, x, v):
+        xp, xk = _ptr(x)
+        vp, vk = _ptr(v)
+        self._call("md_set_state", xp, vp)
+
+    def cells(self):
+        out = np.zeros(self.n, dtype=np.int32)
+        self._call("md_get_cells", out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    def neighbours(self, cap: int = None):
+        cap = int(cap or self.nbr_capacity)
+        counts = np.zeros(self.n, dtype=np.int32)
+        nb = np.full((self.n, cap), -1, dtype=np.int32)
+        self._call("md_get_neighbours", counts.ctypes.data_as(ctypes.c_void_p),
+                   nb.ctypes.data_as(ctypes.c_void_p), cap)
+        return counts, nb
+
+    def check(self):
+        self._call("md_check")
+
+    def set_tuning(self, ctas_per_sm: int = 0, use_graph: int = None):
+        t = B.md_tuning()
+        self._call("md_get_tuning", ctypes.byref(t))
+        if ctas_per_sm:
+            t.ctas_per_sm = int(ctas_per_sm)
+        if use_graph is not None:
+            t.use_graph = int(use_graph)
+        self._call("md_set_tuning", ctypes.byref(t))
+
+    def set_timing(self, enable: bool = True):
+        self._call("md_set_timing", int(bool(enable)))
+
+    def timing(self):
+        """{phase: (ms, calls, launches)} since the last call (waits for the stream)."""
+        ms = np.zeros(B.NPHASE)
+        calls = np.zeros(B.NPHASE, dtype=np.int64)
+        launches = np.zeros(B.NPHASE, dtype=np.int64)
+        self._call("md_get_timing", ms.ctypes.data_as(ctypes.c_void_p), calls.ctypes.data_as(ctypes.c_void_p),
+                   launches.ctypes.data_as(ctypes.c_void_p))
+        return {name: (float(ms[k]), int(calls[k]), int(launches[k])) for k, name in enumerate(B.PHASES)}
+
+    def tuning(self):
+        t = B.md_tuning()
+        self._call("md_get_tuning", ctypes.byref(t))
+        return {k: getattr(t, k) for k, _ in t._fields_}

@@ -1,0 +1,77 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads without a GPU, exports every
+symbol include/gbmd.h declares, and its host-side planning rejects bad parameters."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2003_14061_gb300 import binding as B
+from paper_2003_14061_gb300.system import WCA_RC, make_params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "gbmd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(md_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.lib()
+    syms = header_symbols()
+    assert len(syms) >= 20
+    for name in syms:
+        assert hasattr(L, name), name
+    assert sorted(B.EXPORTS) == syms
+
+
+def test_nvidia_so_is_native_sm103a():
+    path = B.lib_path()
+    assert os.path.exists(path)
+    blob = open(path, "rb").read()
+    assert b"sm_103a" in blob or b"sm_103" in blob
+
+
+def _bytes(**kw):
+    p = make_params(**kw)
+    return B.lib().md_workspace_bytes(ctypes.byref(p))
+
+
+def test_workspace_sizing_and_argument_checks():
+    ok = _bytes(n=2048, box=(13.68, 13.68, 13.68))
+    assert ok > 0 and ok % 256 == 0
+    # bigger systems need more workspace
+    assert _bytes(n=4096, box=(17.2, 17.2, 17.2)) > ok
+    # fewer than 3 cells of side rc + skin
+    assert _bytes(n=100, box=(4.0, 4.0, 4.0)) == 0
+    assert "fewer than 3 cells" in B.last_error()
+    # more than 1023 cells per axis
+    assert _bytes(n=100, box=(2000.0, 10.0, 10.0), skin=0.0) == 0
+    assert "1023" in B.last_error()
+    for bad in (dict(eps=-1.0), dict(dt=0.0), dict(skin=-0.1), dict(precision=7), dict(rebuild_rule=9),
+                dict(reorder_every=-1)):
+        assert _bytes(n=2048, box=(13.68,) * 3, **bad) == 0, bad
+
+
+def test_batch_sizing():
+    L = B.lib()
+    p = make_params()
+    n = np.array([500, 1000, 129], dtype=np.int64)
+    boxes = np.array([[8.5] * 3, [10.7] * 3, [6.0] * 3])
+    nb = L.md_workspace_bytes_batch(ctypes.byref(p), 3, n.ctypes.data_as(ctypes.c_void_p),
+                                    boxes.ctypes.data_as(ctypes.c_void_p))
+    assert nb > 0
+    boxes[2] = 3.0
+    assert L.md_workspace_bytes_batch(ctypes.byref(p), 3, n.ctypes.data_as(ctypes.c_void_p),
+                                      boxes.ctypes.data_as(ctypes.c_void_p)) == 0
+
+
+def test_null_handles_fail_cleanly():
+    L = B.lib()
+    assert L.md_integrate(None, 1) == -1
+    assert L.md_reduce_props(None, None) == -1
+    assert L.md_destroy(None) == -1
+    assert L.md_nrep(None) == 0

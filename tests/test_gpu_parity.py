@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same inputs.
+
+Bars (from the workload definitions):
+  * cell assignment and neighbour sets: bit-exact for identical positions;
+  * step-0 forces: relative L2 error <= 1e-5 (FP32 pair forces), <= 1e-12 (MD_FP64);
+  * 100-step trajectories: max minimum-image position error and relative L2 velocity error
+    <= 1e-4;
+  * energy per particle: absolute difference <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2003_14061_gb300 import binding as B
+from paper_2003_14061_gb300 import inputs
+from paper_2003_14061_gb300.system import WCA_RC, MDSystem
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "mixed", "fp32"]
+
+
+def min_image(d, box):
+    return d - box * np.round(d / box)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def jittered_box(box, counts, amp, seed):
+    """Jittered grid of points in an orthorhombic box (no method arithmetic)."""
+    g = np.stack(np.meshgrid(*[np.arange(c) for c in counts], indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(seed)
+    x = (g + 0.5 + rng.uniform(-amp, amp, g.shape)) * (np.asarray(box) / np.asarray(counts))
+    return np.ascontiguousarray(np.mod(x, box))
+
+
+# name: (x, box, rc, skin, T)
+def case(name):
+    if name == "wca2048":
+        x, box = inputs.fcc_lattice(8, 0.8)
+        return inputs.perturb(x, box, 0.15, 1), box, WCA_RC, 0.4, 1.0
+    if name == "wca1372":           # 10 full tiles and a ragged tail of 92
+        x, box = inputs.fcc_lattice(7, 0.8)
+        return inputs.perturb(x, box, 0.15, 2), box, WCA_RC, 0.4, 1.0
+    if name == "lj1372":
+        x, box = inputs.fcc_lattice(7, 0.8442)
+        return inputs.perturb(x, box, 0.08, 3), box, 2.5, 0.3, 0.72
+    if name == "ortho":
+        box = np.array([9.0, 7.5, 12.0])
+        return jittered_box(box, (8, 6, 11), 0.2, 4), box, WCA_RC, 0.35, 1.0
+    raise KeyError(name)
+
+
+CASES = ["wca2048", "wca1372", "lj1372", "ortho"]
+
+
+def make(name, prec, **kw):
+    x, box, rc, skin, T = case(name)
+    v = inputs.maxwell(x.shape[0], T, seed=5)
+    kw.setdefault("reorder_every", 100)
+    s = MDSystem(x, v, box, rc=rc, skin=skin, precision=prec, **kw)
+    return s, x, v, box, rc, skin
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", CASES)
+def test_cells_bit_exact(name, prec):
+    s, x, v, box, rc, skin = make(name, prec)
+    nc, cell = oracle.cells(x, box, rc + skin)
+    assert np.array_equal(s.cells_per_axis(), nc)
+    assert np.array_equal(s.cells(), cell)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", CASES)
+def test_neighbour_sets_bit_exact(name, prec):
+    s, x, v, box, rc, skin = make(name, prec)
+    counts, nb = s.neighbours()
+    _, oc, off, onb = oracle.neighbours(x, box, rc, skin, fp32=(prec != "fp64"))
+    assert np.array_equal(counts, oc)
+    for i in range(x.shape[0]):
+        assert np.array_equal(np.sort(nb[i, : counts[i]]), onb[off[i]: off[i + 1]]), i
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", CASES)
+def test_step0_forces_and_energy(name, prec):
+    s, x, v, box, rc, skin = make(name, prec)
+    _, _, f = s.state(x=False, v=False, f=True)
+    p = oracle.pot(rc=rc)
+    of, ua, U, W = oracle.forces(x, box, p)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert rel_l2(f, of) <= tol
+    pr = s.props()[0]
+    op = oracle.props(x, v, box, p)
+    n = x.shape[0]
+    assert abs(pr["U"] - op[0]) / n <= 1e-6
+    assert abs(pr["K"] - op[1]) / n <= 1e-6
+    assert abs(pr["E_per_atom"] - (op[0] + op[1]) / n) <= 1e-6
+    assert abs(pr["virial"] - op[2]) / n <= 1e-5
+    assert abs(pr["pressure"] - op[3]) <= 1e-6
+    assert np.abs(np.array(pr["P"]) - op[4:7]).max() <= 1e-9 * n
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["wca2048", "wca1372", "lj1372"])
+def test_trajectory_100_steps(name, prec):
+    s, x, v, box, rc, skin = make(name, prec)
+    s.integrate(100)
+    xg, vg, _ = s.state()
+    p = oracle.pot(rc=rc)
+    xo, vo, po, rb = oracle.run(x, v, box, p, dt=0.005, nsteps=100, rule=1, skin=skin)
+    assert np.abs(min_image(xg - xo, box)).max() <= 1e-4
+    assert rel_l2(vg, vo) <= 1e-4
+    pr = s.props()[0]
+    n = x.shape[0]
+    assert abs(pr["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / n) <= 1e-6
+    assert pr["step"] == 100
+    assert abs(pr["rebuilds"] - (rb + 1)) <= 2         # +1: the build at creation
+
+
+def test_repeat_runs_bit_identical():
+    a, x, v, box, rc, skin = make("wca1372", "mixed")
+    b, *_ = make("wca1372", "mixed")
+    a.integrate(300)
+    b.integrate(300)
+    xa, va, _ = a.state()
+    xb, vb, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_energy_conservation_matches_oracle():
+    s, x, v, box, rc, skin = make("wca2048", "mixed", props_every=10)
+    s.integrate(1000)
+    ser = s.series()[0]
+    E = ser[:, 1] + ser[:, 2]
+    p = oracle.pot(rc=rc)
+    _, _, po, _ = oracle.run(x, v, box, p, dt=0.005, nsteps=1000)
+    Eo = po[::10, 0] + po[::10, 1]
+    assert ser.shape[0] == 100 and np.array_equal(ser[:, 0], np.arange(0, 1000, 10))
+    n = x.shape[0]
+    # same conserved-energy behaviour (bounded, O(dt^2)) -- the trajectories decorrelate by chaos
+    assert np.abs(E - E[0]).max() / abs(E[0]) < 2.0 * np.abs(Eo - Eo[0]).max() / abs(Eo[0]) + 1e-5
+    assert abs(E[0] - Eo[0]) / n <= 1e-6
+
+
+def test_rebuild_rules():
+    for rule in ("vmax", "disp", "every"):
+        s, x, v, box, rc, skin = make("wca1372", "mixed", rebuild_rule=rule)
+        s.integrate(60)
+        xg, vg, _ = s.state()
+        xo, vo, _, rb = oracle.run(x, v, box, oracle.pot(rc=rc), dt=0.005, nsteps=60, rule=0)
+        assert np.abs(min_image(xg - xo, box)).max() <= 1e-4, rule
+        pr = s.props()[0]
+        if rule == "every":
+            assert pr["rebuilds"] == 61
+        elif rule == "disp":
+            _, _, _, rbd = oracle.run(x, v, box, oracle.pot(rc=rc), dt=0.005, nsteps=60, rule=2, skin=skin)
+            assert abs(pr["rebuilds"] - (rbd + 1)) <= 1
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_batched_replicas(prec):
+    specs = inputs.replica_specs(7, 500, 3000, 0.6, 0.9, seed=4)
+    states = inputs.replica_states(specs, 1.0, seed=4)
+    n_rep = [sp[0] for sp in specs]
+    boxes = np.stack([st[2] for st in states])
+    x = np.concatenate([st[0] for st in states])
+    v = np.concatenate([st[1] for st in states])
+    s = MDSystem(x, v, n_rep=n_rep, boxes=boxes, rc=WCA_RC, skin=0.4, precision=prec)
+    _, _, f = s.state(x=False, v=False, f=True)
+    s.integrate(50)
+    xg, vg, _ = s.state()
+    props = s.props()
+    off = 0
+    p = oracle.pot()
+    for r, (xr, vr, br) in enumerate(states):
+        n = xr.shape[0]
+        of, _, _, _ = oracle.forces(xr, br, p)
+        assert rel_l2(f[off:off + n], of) <= 1e-5
+        xo, vo, po, _ = oracle.run(xr, vr, br, p, dt=0.005, nsteps=50)
+        assert np.abs(min_image(xg[off:off + n] - xo, br)).max() <= 1e-4
+        assert rel_l2(vg[off:off + n], vo) <= 1e-4
+        assert abs(props[r]["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / n) <= 1e-6
+        off += n
+
+
+def test_neighbour_overflow_is_reported():
+    x, box, rc, skin, T = case("wca1372")
+    v = inputs.maxwell(x.shape[0], T, seed=5)
+    with pytest.raises(B.MDError) as e:
+        MDSystem(x, v, box, rc=rc, skin=skin, nbr_capacity=4)
+    assert e.value.status == "MD_ERR_NBR_OVERFLOW"
+
+
+def test_small_workspace_is_rejected():
+    import ctypes
+    from paper_2003_14061_gb300.system import make_params
+    x, box, rc, skin, T = case("wca1372")
+    v = inputs.maxwell(x.shape[0], T, seed=5)
+    p = make_params(n=x.shape[0], box=box, rc=rc, skin=skin)
+    L = B.lib()
+    need = L.md_workspace_bytes(ctypes.byref(p))
+    ws = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    rc_ = L.md_create(ctypes.byref(p), ctypes.c_void_p(ws.data_ptr()), need // 2,
+                      x.ctypes.data_as(ctypes.c_void_p), v.ctypes.data_as(ctypes.c_void_p),
+                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(h))
+    assert B.STATUS[rc_] == "MD_ERR_WORKSPACE"
+
+
+# ---------------------------------------------------------------------------------------------
+# full-size workloads: sampled outputs
+# ---------------------------------------------------------------------------------------------
+FULL = {
+    "wca_4M": dict(ncell=100, rho=0.8, rc=WCA_RC, skin=0.4, T=1.0),
+    "lj_16M": dict(ncell=160, rho=0.8442, rc=2.5, skin=0.3, T=0.72),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_sampled(name):
+    c = FULL[name]
+    x, box = inputs.fcc_lattice(c["ncell"], c["rho"])
+    x = inputs.perturb(x, box, 0.1, 7)
+    n = x.shape[0]
+    v = inputs.maxwell(n, c["T"], seed=8)
+    s = MDSystem(x, v, box, rc=c["rc"], skin=c["skin"], precision="mixed", reorder_every=100)
+    nc, cell = oracle.cells(x, box, c["rc"] + c["skin"])
+    assert np.array_equal(s.cells(), cell)
+    rng = np.random.default_rng(9)
+    sample = np.sort(rng.choice(n, 3000, replace=False))
+    counts, nb = s.neighbours()
+    cap = s.nbr_capacity
+    oc, onb = oracle.neighbours_sample(x, box, c["rc"], c["skin"], sample, cap, fp32=True)
+    assert np.array_equal(counts[sample], oc)
+    for k, i in enumerate(sample):
+        assert np.array_equal(np.sort(nb[i, : counts[i]]), onb[k, : oc[k]])
+    _, _, f = s.state(x=False, v=False, f=True)
+    of, _ = oracle.force_on_atoms(x, box, oracle.pot(rc=c["rc"]), sample)
+    assert rel_l2(f[sample], of) <= 1e-5
+    p0 = s.props()[0]
+    s.integrate(20)
+    p1 = s.props()[0]
+    assert abs(p1["E_per_atom"] - p0["E_per_atom"]) < 1e-3 * abs(p0["E_per_atom"])
+    assert np.abs(np.array(p1["P"]) - np.array(p0["P"])).max() < 1e-6 * n
+    s.close()
