@@ -102,8 +102,12 @@ def test_step0_forces_and_energy(name, prec):
     assert abs(pr["K"] - op[1]) / n <= 1e-6
     assert abs(pr["E_per_atom"] - (op[0] + op[1]) / n) <= 1e-6
     assert abs(pr["virial"] - op[2]) / n <= 1e-5
-    assert abs(pr["pressure"] - op[3]) <= 1e-6
-    assert np.abs(np.array(pr["P"]) - op[4:7]).max() <= 1e-9 * n
+    # P = (2K + W) / 3V: the virial bound carries over as |dP| <= 1e-5 n / 3V
+    assert abs(pr["pressure"] - op[3]) <= 1e-5 * n / (3.0 * np.prod(box))
+    # FP32 state rounds each velocity component by at most 2^-24 |v|, so the total momentum of
+    # the stored velocities can differ from the FP64 input's by sum |v| 2^-24
+    ptol = np.abs(v).sum(0) * 2.0 ** -24 + 1e-12 * n if prec == "fp32" else 1e-9 * n
+    assert np.all(np.abs(np.array(pr["P"]) - op[4:7]) <= ptol)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -166,7 +170,9 @@ def test_rebuild_rules():
 @pytest.mark.parametrize("prec", ["mixed", "fp32"])
 def test_batched_replicas(prec):
     specs = inputs.replica_specs(7, 500, 3000, 0.6, 0.9, seed=4)
-    states = inputs.replica_states(specs, 1.0, seed=4)
+    # perturbed so that every replica starts with non-zero forces
+    states = [(inputs.perturb(xr, br, 0.08, 40 + r), vr, br)
+              for r, (xr, vr, br) in enumerate(inputs.replica_states(specs, 1.0, seed=4))]
     n_rep = [sp[0] for sp in specs]
     boxes = np.stack([st[2] for st in states])
     x = np.concatenate([st[0] for st in states])
