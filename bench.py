@@ -51,7 +51,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def make_inputs(name, rank=0):
+def make_inputs(name, rank=0, ncell=0):
     from paper_2003_14061_gb300 import inputs
     w = WORKLOADS[name]
     seed = SEED[name] + 1000 * rank
@@ -61,7 +61,7 @@ def make_inputs(name, rank=0):
         x = np.concatenate([s[0] for s in states])
         v = np.concatenate([s[1] for s in states])
         return x, v, dict(n_rep=[s[0] for s in specs], boxes=np.stack([s[2] for s in states]))
-    x, box = inputs.fcc_lattice(w["ncell"], w["rho"])
+    x, box = inputs.fcc_lattice(ncell or w["ncell"], w["rho"])
     v = inputs.maxwell(x.shape[0], w["T"], seed)
     return x, v, dict(box=box)
 
@@ -148,7 +148,7 @@ def run_gb300(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = WORKLOADS[args.workload]
-    x, v, geo = make_inputs(args.workload, rank)
+    x, v, geo = make_inputs(args.workload, rank, args.ncell)
     n = x.shape[0]
     s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
                  rebuild_rule="vmax", **geo)
@@ -158,14 +158,14 @@ def run_gb300(args, rank, world, local_rank):
     # warm-up (also melts the lattice: timed steps see a fluid)
     s.integrate(args.warmup)
     torch.cuda.synchronize()
-    s.timing()                                  # reset counters
-    s.set_timing(True)
+    rb0 = [p["rebuilds"] for p in s.props()]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    s.timing()                                  # reset launch counters
     with ClockSampler(local_rank) as clk:
         e0.record(stream)
         s.integrate(args.steps)
@@ -174,11 +174,17 @@ def run_gb300(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    phases = s.timing()
-    s.set_timing(False)
+    issued = s.timing()
     props = s.props()
+    rebuilds_timed = sum(p["rebuilds"] - r0 for p, r0 in zip(props, rb0))
+    # kernels that ran: the host-issued ones plus, inside captured graphs, the 10 kernels of
+    # every rebuild whose IF node opened (a batch runs one rebuild sequence for all replicas)
+    graph_mode = s.tuning()["use_graph"] == 1
+    launches = sum(p[2] for p in issued.values())
+    if graph_mode:
+        nrb = max(p["rebuilds"] - r0 for p, r0 in zip(props, rb0)) if s.nrep == 1 else rebuilds_timed
+        launches += 10 * int(nrb)
     mean_nbrs = float(np.average([p["mean_nbrs"] for p in props], weights=s.n_rep))
-    rebuilds = sum(p["rebuilds"] for p in props) / len(props)
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -186,13 +192,19 @@ def run_gb300(args, rank, world, local_rank):
     total_atoms = n * world
     value = total_atoms * args.steps / (ms * 1e-3)
 
-    # roofline of the dominant kernel (the fused force + leapfrog step)
+    # per-kernel durations: the same workload continued with direct launches, every phase
+    # bracketed by CUDA events on the library's stream (graph replays cannot be split per kernel)
+    s.set_tuning(use_graph=2)
+    s.set_timing(True)
+    s.integrate(min(args.steps, args.phase_steps))
+    phases = s.timing()
+    s.set_timing(False)
+    s.set_tuning(use_graph=1)
     step_ms, step_calls, step_launches = phases["step"]
     peak, peak_kind = load_peaks()
     bpa = algorithmic_bytes_per_atom_step(mean_nbrs)
     per_launch_ms = step_ms / max(step_calls, 1)
     achieved = bpa * n / (per_launch_ms * 1e-3) / 1e9
-    launches = sum(p[2] for p in phases.values())
 
     # end to end through the public API with host buffers: pinned H2D of the state, K steps each
     # followed by a D2H read of that step's props, and a D2H read of the final state
@@ -239,11 +251,14 @@ def run_gb300(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": w["desc"], "atoms_per_gpu": n, "precision": "FP32 pair forces, FP64 state",
+            "config": {"workload": w["desc"] if not args.ncell else f"{w['desc']} (resized: fcc {args.ncell}^3)",
+                       "atoms_per_gpu": n, "precision": "FP32 pair forces, FP64 state",
                        "skin": w["skin"], "rc": w["rc"], "dt": DT, "reorder_every": 100,
                        "rebuild_rule": "max-velocity bound > skin/2",
                        "l2": "inputs larger than L2 (state %.2f GB)" % (s.workspace_bytes / 1e9),
-                       "mean_neighbours": mean_nbrs, "rebuilds_per_100_steps": None},
+                       "mean_neighbours": mean_nbrs,
+                       "rebuilds_per_100_steps": 100.0 * rebuilds_timed / max(s.nrep, 1) / args.steps,
+                       "cuda_graph": graph_mode},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_step<MD_MIXED>",
                          "bytes_per_atom": bpa, "peak_kind": peak_kind},
@@ -252,8 +267,9 @@ def run_gb300(args, rank, world, local_rank):
                     "d2h_bytes_per_step": props_bytes + 48.0 * total_atoms / e2e_steps, "steps": e2e_steps},
             "gpu_launches": launches,
             "clocks": clk.summary(),
-            "phases_ms": {k: round(vv[0], 3) for k, vv in phases.items()},
-            "phase_launches": {k: vv[2] for k, vv in phases.items()},
+            "phases_ms_direct": {k: round(vv[0], 3) for k, vv in phases.items()},
+            "phase_steps_direct": min(args.steps, args.phase_steps),
+            "kernel_ms_per_launch": per_launch_ms,
         }
     s.close()
     return result
@@ -304,7 +320,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="wca4m", choices=list(WORKLOADS))
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--ncell", type=int, default=0, help="fcc cells per axis (smaller case for profiling)")
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--phase-steps", type=int, default=400)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -177,13 +177,14 @@ int64_t md_natoms(const md_system* s);
 int32_t md_nbr_capacity(const md_system* s);
 int md_cells_per_axis(const md_system* s, int32_t r, int32_t* nc);
 
-/* Launch shapes chosen by the autotuner (threads per block of the step and build kernels,
- * persistent CTAs per SM).  0 keeps the current value. */
+/* Launch shapes chosen by the autotuner (paper_2003_14061_gb300.tune): the paper found block
+ * size mattered little on its GPU and warned that this need not hold in general (Sec. 4.1
+ * item 2).  A field left 0 keeps its current value. */
 typedef struct {
-    int32_t step_block;      /* 64..1024, multiple of 32 */
-    int32_t build_block;     /* 64..1024, multiple of 32 */
-    int32_t ctas_per_sm;     /* persistent grid size = SMs * ctas_per_sm */
-    int32_t use_graph;       /* 1: replay md_integrate from captured CUDA graphs */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM for the tile loops (1..64); grid = SMs x this */
+    int32_t nbr_batch;       /* W entries each thread loads together in the pair loop: 2, 4 or 8 */
+    int32_t build_batch;     /* candidate atoms each thread loads together in the build: 1, 2 or 4 */
+    int32_t use_graph;       /* 1: md_integrate replays captured CUDA graphs; 2: direct launches */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);

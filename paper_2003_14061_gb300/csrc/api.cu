@@ -209,6 +209,25 @@ struct md_system {
     int64_t calls[MD_NPHASE] = {0};
     int64_t launches[MD_NPHASE] = {0};
 
+    // CUDA graphs of GRAPH_STEPS steps each (one per starting position buffer)
+    static constexpr int GRAPH_STEPS = 16;
+    cudaStream_t aux = nullptr;       // captures the IF-node bodies
+    cudaStream_t gstream = nullptr;   // captures and replays the graphs (the caller's stream may be
+                                      // the legacy default stream, which cannot be captured)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+
+    void drop_graphs()
+    {
+        for (int b = 0; b < 2; ++b) {
+            if (gexec[b]) cudaGraphExecDestroy(gexec[b]);
+            if (graph[b]) cudaGraphDestroy(graph[b]);
+            gexec[b] = nullptr;
+            graph[b] = nullptr;
+        }
+    }
+
     cudaEvent_t take_event()
     {
         if (!pool.empty()) {
@@ -224,6 +243,11 @@ struct md_system {
     {
         for (auto& pr : pending) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
         for (auto e : pool) cudaEventDestroy(e);
+        drop_graphs();
+        if (aux) cudaStreamDestroy(aux);
+        if (gstream) cudaStreamDestroy(gstream);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
     }
 };
 
@@ -303,6 +327,8 @@ int apply_tuning(md_system* s)
     s->L.grid = std::max(1, s->nsm * per_sm);
     s->L.step_block = TILE;
     s->L.build_block = TILE;
+    s->L.nbr_batch = s->tune.nbr_batch;
+    s->L.build_batch = s->tune.build_batch;
     return MD_OK;
 }
 
@@ -334,6 +360,79 @@ int load_state(md_system* s, const double* x, const double* v)
     GBMD_CUDA(launch_rebuild(s->A, s->S, s->L, s->cur, true));
     s->host_step = 0;
     s->binned_fresh = false;
+    return MD_OK;
+}
+
+// Capture GRAPH_STEPS steps starting from position buffer cur0: each step is the fused step
+// kernel followed by an IF node whose body is the rebuild sequence; the step kernel opens the IF
+// node only when some replica's refresh criterion fired, so steps without a rebuild launch
+// nothing but the step kernel.
+int capture_graph(md_system* s, int cur0)
+{
+    if (!s->aux) GBMD_CUDA(cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
+    if (!s->gstream) GBMD_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+    if (!s->ev_in) GBMD_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+    if (!s->ev_out) GBMD_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+    cudaStream_t st = s->gstream;
+    GBMD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    int cur = cur0;
+    for (int k = 0; k < md_system::GRAPH_STEPS && err == cudaSuccess; ++k) {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* ed = nullptr;
+        size_t nd = 0;
+        err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
+        cudaGraphConditionalHandle h = 0;
+        if (err == cudaSuccess) err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        Launch L = s->L;
+        L.stream = st;
+        L.cond = h;
+        L.use_cond = 1;
+        if (err == cudaSuccess) err = launch_step(s->A, s->S, L, cur, false);
+        cur ^= 1;
+        if (err == cudaSuccess) err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (err == cudaSuccess) err = cudaGraphAddNode(&node, g, deps, ed, nd, &cp);
+        if (err == cudaSuccess)
+            err = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (err == cudaSuccess)
+            err = cudaStreamBeginCaptureToGraph(s->aux, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+        if (err == cudaSuccess) {
+            Launch Lb = s->L;
+            Lb.stream = s->aux;
+            Lb.use_cond = 0;
+            cudaError_t e2 = launch_bin_order(s->A, s->S, Lb, cur, false);
+            if (e2 == cudaSuccess) e2 = launch_reorder(s->A, s->S, Lb, cur);
+            if (e2 == cudaSuccess) e2 = launch_build_only(s->A, s->S, Lb, cur);
+            cudaGraph_t body = nullptr;
+            err = cudaStreamEndCapture(s->aux, &body);
+            if (err == cudaSuccess) err = e2;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e_end = cudaStreamEndCapture(st, &graph);
+    if (err == cudaSuccess) err = e_end;
+    if (err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(MD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(err));
+    }
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(MD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
+    }
+    s->graph[cur0] = graph;
+    s->gexec[cur0] = exec;
     return MD_OK;
 }
 
@@ -394,10 +493,10 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     cudaError_t e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
     s->nsm = prop.multiProcessorCount;
-    s->tune.step_block = TILE;
-    s->tune.build_block = TILE;
-    s->tune.ctas_per_sm = 8;
-    s->tune.use_graph = 0;
+    s->tune.ctas_per_sm = 12;
+    s->tune.nbr_batch = 4;
+    s->tune.build_batch = 2;
+    s->tune.use_graph = 1;
     apply_tuning(s);
 
     auto bail = [&](int code) { delete s; return code; };
@@ -469,7 +568,26 @@ int md_integrate(md_system* s, int32_t nsteps)
         GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
         s->binned_fresh = false;
     }
-    for (int32_t k = 0; k < nsteps; ++k) {
+    int32_t k = 0;
+    if (s->tune.use_graph == 1 && s->p.props_every == 0) {
+        const int G = md_system::GRAPH_STEPS;
+        while (k + G <= nsteps) {
+            if (!s->gexec[s->cur]) {
+                const int rc = capture_graph(s, s->cur);
+                if (rc) return rc;
+            }
+            Phase t(s, MD_PHASE_STEP, G);
+            // replay on the library's stream, ordered after and before the caller's stream
+            GBMD_CUDA(cudaEventRecord(s->ev_in, s->L.stream));
+            GBMD_CUDA(cudaStreamWaitEvent(s->gstream, s->ev_in, 0));
+            GBMD_CUDA(cudaGraphLaunch(s->gexec[s->cur], s->gstream));
+            GBMD_CUDA(cudaEventRecord(s->ev_out, s->gstream));
+            GBMD_CUDA(cudaStreamWaitEvent(s->L.stream, s->ev_out, 0));
+            k += G;
+            s->host_step += G;
+        }
+    }
+    for (; k < nsteps; ++k) {
         const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
         {
             Phase t(s, MD_PHASE_STEP, props ? 2 : 1);
@@ -640,11 +758,17 @@ int md_cells_per_axis(const md_system* s, int32_t r, int32_t* nc)
 int md_set_tuning(md_system* s, const md_tuning* t)
 {
     if (!s || !t) return fail(MD_ERR_INVALID_ARG, "bad arguments");
-    if (t->step_block && t->step_block != TILE) return fail(MD_ERR_INVALID_ARG, "step_block must be 128");
-    if (t->build_block && t->build_block != TILE) return fail(MD_ERR_INVALID_ARG, "build_block must be 128");
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(MD_ERR_INVALID_ARG, "ctas_per_sm in 0..64");
+    if (t->nbr_batch && t->nbr_batch != 2 && t->nbr_batch != 4 && t->nbr_batch != 8)
+        return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 2, 4 or 8");
+    if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4)
+        return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2 or 4");
+    if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
-    s->tune.use_graph = t->use_graph;
+    if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
+    if (t->build_batch) s->tune.build_batch = t->build_batch;
+    if (t->use_graph) s->tune.use_graph = t->use_graph;
+    s->drop_graphs();          // launch shapes are baked into captured graphs
     return apply_tuning(s);
 }
 

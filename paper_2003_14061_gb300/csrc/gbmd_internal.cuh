@@ -188,6 +188,10 @@ struct Launch {
     int grid;                 // persistent CTAs for tile loops
     int step_block;
     int build_block;
+    int nbr_batch;            // W entries loaded together per thread in the pair loop (2, 4, 8)
+    int build_batch;          // candidates loaded together per thread in the build (1, 2, 4)
+    cudaGraphConditionalHandle cond;   // IF node of the rebuild (inside a captured graph)
+    int use_cond;             // 1 while capturing md_integrate into a graph
 };
 
 // rebuild path (kernels_rebuild.cu)

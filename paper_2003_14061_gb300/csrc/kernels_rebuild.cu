@@ -39,29 +39,15 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         const int64_t j = slot - R.slot0;
         int occ = 0;
-        if (j < R.n) {
-            double x[3];
-            uint32_t pw;
-            if (from_set) {            // md_set_state left global positions in xl, origin (0,0,0)
-                x[0] = A.xl[0][slot]; x[1] = A.xl[1][slot]; x[2] = A.xl[2][slot];
-                pw = 0u;
-            } else if (MODE == MD_FP32) {
-                const float4 p = A.pos32[cur][slot];
-                x[0] = p.x; x[1] = p.y; x[2] = p.z;
-                pw = __float_as_uint(p.w);
-            } else {
-                x[0] = A.xl[0][slot]; x[1] = A.xl[1][slot]; x[2] = A.xl[2][slot];
-                pw = (MODE == MD_FP64) ? cell_bits(A.pos64[cur][slot].w)
-                                       : __float_as_uint(A.pos32[cur][slot].w);
-            }
-            int oc[3];
-            unpack_cell(pw, oc[0], oc[1], oc[2]);
+        if (j < R.n && from_set) {
+            // exact binning of a global position (the definition the oracle follows):
+            // wrap into [0, L), c = floor(x n_c / L) clamped, local = x - c w, all in FP64
+            double x[3] = {A.xl[0][slot], A.xl[1][slot], A.xl[2][slot]};
             int c[3];
             double loc[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                // global coordinate, wrapped once into [0, L)
-                double xa = __dadd_rn(__dmul_rn(double(oc[a]), R.w[a]), x[a]);
+                double xa = x[a];
                 if (xa < 0.0) xa = __dadd_rn(xa, R.L[a]);
                 if (xa >= R.L[a]) xa = __dsub_rn(xa, R.L[a]);
                 int ca = int(floor(__dmul_rn(xa, R.s[a])));
@@ -81,6 +67,68 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
             }
             const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
             A.cell[slot] = cell;
+            const int l = atomicAdd(&A.ccount[cell], 1);
+            A.layer[slot] = l;
+            occ = l + 1;
+        } else if (j < R.n) {
+            // during a run every atom is within skin/2 < w of its cell: it stays or moves to the
+            // adjacent cell along each axis; its local coordinate shifts by -s w (s in -1, 0, 1)
+            int c[3], sh[3];
+            bool moved = false;
+            if (MODE == MD_FP64) {
+                const double4_32a p = A.pos64[cur][slot];
+                unpack_cell(cell_bits(p.w), c[0], c[1], c[2]);
+                const double l[3] = {p.x, p.y, p.z};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    sh[a] = (l[a] < 0.0) ? -1 : ((l[a] >= R.w[a]) ? 1 : 0);
+                    moved |= sh[a] != 0;
+                    if (!(l[a] >= -R.w[a] && l[a] < 2.0 * R.w[a])) atomicOr(&A.g->err, ERR_NONFINITE);
+                }
+                if (moved) {
+                    double nl[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        nl[a] = sh[a] ? __dsub_rn(l[a], double(sh[a]) * R.w[a]) : l[a];
+                        int ca = c[a] + sh[a];
+                        ca += (ca < 0) ? R.nc[a] : 0;
+                        ca -= (ca >= R.nc[a]) ? R.nc[a] : 0;
+                        c[a] = ca;
+                        A.xl[a][slot] = nl[a];
+                    }
+                    A.pos64[cur][slot] = make_double4_32a(nl[0], nl[1], nl[2], cell_word_d(pack_cell(c[0], c[1], c[2])));
+                }
+            } else {
+                const float4 p = A.pos32[cur][slot];
+                unpack_cell(__float_as_uint(p.w), c[0], c[1], c[2]);
+                const float l[3] = {p.x, p.y, p.z};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    sh[a] = (l[a] < 0.0f) ? -1 : ((l[a] >= R.wf[a]) ? 1 : 0);
+                    moved |= sh[a] != 0;
+                    if (!(l[a] >= -R.wf[a] && l[a] < 2.0f * R.wf[a])) atomicOr(&A.g->err, ERR_NONFINITE);
+                }
+                if (moved) {
+                    float nl[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (MODE == MD_MIXED) {
+                            const double x = sh[a] ? __dsub_rn(A.xl[a][slot], double(sh[a]) * R.w[a]) : A.xl[a][slot];
+                            if (sh[a]) A.xl[a][slot] = x;
+                            nl[a] = __double2float_rn(x);
+                        } else {
+                            nl[a] = sh[a] ? __fsub_rn(l[a], float(sh[a]) * R.wf[a]) : l[a];
+                        }
+                        int ca = c[a] + sh[a];
+                        ca += (ca < 0) ? R.nc[a] : 0;
+                        ca -= (ca >= R.nc[a]) ? R.nc[a] : 0;
+                        c[a] = ca;
+                    }
+                    A.pos32[cur][slot] = make_float4(nl[0], nl[1], nl[2], cell_word_f(pack_cell(c[0], c[1], c[2])));
+                }
+            }
+            const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+            if (moved) A.cell[slot] = cell;
             const int l = atomicAdd(&A.ccount[cell], 1);
             A.layer[slot] = l;
             occ = l + 1;
@@ -296,7 +344,7 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-template <typename T>
+template <typename T, int BB>
 __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
 {
     using P4 = typename PosT<T>::type;
@@ -319,29 +367,45 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
             T w[3];
             if constexpr (sizeof(T) == 8) { w[0] = R.w[0]; w[1] = R.w[1]; w[2] = R.w[2]; }
             else { w[0] = R.wf[0]; w[1] = R.wf[1]; w[2] = R.wf[2]; }
+            const int xm = (cx == 0) ? R.nc[0] - 1 : cx - 1;
+            const int xp = (cx == R.nc[0] - 1) ? 0 : cx + 1;
             for (int oz = -1; oz <= 1; ++oz) {
                 int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
                 const T offz = T(oz) * w[2];
                 for (int oy = -1; oy <= 1; ++oy) {
                     int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
                     const T offy = T(oy) * w[1];
-                    for (int ox = -1; ox <= 1; ++ox) {
-                        int nx = cx + ox; nx += (nx < 0) ? R.nc[0] : 0; nx -= (nx >= R.nc[0]) ? R.nc[0] : 0;
-                        const T offx = T(ox) * w[0];
-                        const int gc = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0] + nx;
-                        const uint32_t code = (uint32_t(ox + 1) | (uint32_t(oy + 1) << 2) |
-                                               (uint32_t(oz + 1) << 4)) << 26;
-                        const int kb = A.cstart[gc], ke = A.cstart[gc + 1];
-                        for (int k = kb; k < ke; ++k) {
-                            const int32_t jslot = A.perm[k];
-                            if (jslot == slot) continue;
-                            const P4 pj = pos[jslot];
-                            const T dx = add_rn(sub_rn(pj.x, pi.x), offx);
-                            const T dy = add_rn(sub_rn(pj.y, pi.y), offy);
-                            const T dz = add_rn(sub_rn(pj.z, pi.z), offz);
+                    const int row = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0];
+                    // the three cells of this row, as [b0,e0) [b1,e1) [b2,e2) in perm
+                    const int b0 = A.cstart[row + xm], e0 = A.cstart[row + xm + 1];
+                    const int b1 = A.cstart[row + cx], e1 = A.cstart[row + cx + 1];
+                    const int b2 = A.cstart[row + xp], e2 = A.cstart[row + xp + 1];
+                    const int n0 = e0 - b0, n01 = n0 + (e1 - b1), ntot = n01 + (e2 - b2);
+                    const uint32_t codeyz = ((uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4)) << 26;
+                    for (int q0 = 0; q0 < ntot; q0 += BB) {
+                        int32_t js[BB];
+#pragma unroll
+                        for (int u = 0; u < BB; ++u) {
+                            const int q = q0 + u;
+                            const int k = (q < n0) ? b0 + q : ((q < n01) ? b1 + (q - n0) : b2 + (q - n01));
+                            js[u] = (q < ntot) ? A.perm[k] : -1;
+                        }
+                        P4 pj[BB];
+#pragma unroll
+                        for (int u = 0; u < BB; ++u) pj[u] = (js[u] >= 0) ? pos[js[u]] : pi;
+#pragma unroll
+                        for (int u = 0; u < BB; ++u) {
+                            const int q = q0 + u;
+                            if (js[u] < 0 || js[u] == slot) continue;
+                            const int ox = (q < n0) ? -1 : ((q < n01) ? 0 : 1);
+                            const T offx = T(ox) * w[0];
+                            const T dx = add_rn(sub_rn(pj[u].x, pi.x), offx);
+                            const T dy = add_rn(sub_rn(pj[u].y, pi.y), offy);
+                            const T dz = add_rn(sub_rn(pj[u].z, pi.z), offz);
                             const T r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                             if (r2 < rl2) {
-                                if (m < S.cap) A.W[int64_t(m) * S.nslots + slot] = uint32_t(jslot) | code;
+                                if (m < S.cap)
+                                    A.W[int64_t(m) * S.nslots + slot] = uint32_t(js[u]) | codeyz | (uint32_t(ox + 1) << 26);
                                 ++m;
                             }
                         }
@@ -458,8 +522,10 @@ cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int
 cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur)
 {
     const int g = tile_grid(S, L);
-    if (S.mode == MD_FP64) k_build<double><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    else k_build<float><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    if (S.mode == MD_FP64) k_build<double, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (L.build_batch >= 4) k_build<float, 4><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (L.build_batch >= 2) k_build<float, 2><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else k_build<float, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
     k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S);
     return cudaGetLastError();
 }

@@ -31,34 +31,51 @@ __device__ __forceinline__ float offset_f(uint32_t code2)
 struct AccF { float fx, fy, fz, u, w; };
 struct AccD { double fx, fy, fz, u, w; };
 
+// One thread per atom over its column of W, NB entries at a time: the NB row loads are issued
+// together, then the NB position gathers, so each thread keeps 2 NB loads in flight.
+template <int NB>
 __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const Rep& R,
                                           const float4* __restrict__ pos, int64_t slot, float4 pi)
 {
     AccF a{0.f, 0.f, 0.f, 0.f, 0.f};
-    const int mm = min(A.nbr_count[slot], S.cap);
+    const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
     const uint32_t* __restrict__ Wc = A.W + slot;
     const float wx = R.wf[0], wy = R.wf[1], wz = R.wf[2];
-#pragma unroll 4
-    for (int m = 0; m < mm; ++m) {
-        const uint32_t e = __ldcs(Wc + int64_t(m) * S.nslots);
-        const float4 pj = __ldg(pos + (e & IDX_MASK));
-        const float dx = fmaf(offset_f((e >> 26) & 3u), wx, pj.x - pi.x);
-        const float dy = fmaf(offset_f((e >> 28) & 3u), wy, pj.y - pi.y);
-        const float dz = fmaf(offset_f(e >> 30), wz, pj.z - pi.z);
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (r2 < S.rc2f) {
-            const float ri2 = __frcp_rn(r2);
-            const float sr2 = S.sig2f * ri2;
-            const float sr6 = sr2 * sr2 * sr2;
-            const float fs = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;   // g(r^2)
-            a.fx = fmaf(-fs, dx, a.fx);                              // f_i = g (x_i - x_j)
-            a.fy = fmaf(-fs, dy, a.fy);
-            a.fz = fmaf(-fs, dz, a.fz);
-            a.u += fmaf(S.eps4f * sr6, sr6 - 1.0f, -S.ucf);
-            a.w = fmaf(fs, r2, a.w);
+    for (int m0 = 0; m0 < mm; m0 += NB) {
+        uint32_t e[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            e[k] = (m0 + k < mm) ? __ldcs(Wc + int64_t(m0 + k) * S.nslots) : 0u;
+        float4 pj[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k)
+            pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] & IDX_MASK)) : pi;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t ek = e[k];
+            const float dx = fmaf(offset_f((ek >> 26) & 3u), wx, pj[k].x - pi.x);
+            const float dy = fmaf(offset_f((ek >> 28) & 3u), wy, pj[k].y - pi.y);
+            const float dz = fmaf(offset_f(ek >> 30), wz, pj[k].z - pi.z);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (m0 + k < mm && r2 < S.rc2f) {
+                const float ri2 = __frcp_rn(r2);
+                const float sr2 = S.sig2f * ri2;
+                const float sr6 = sr2 * sr2 * sr2;
+                const float fs = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;   // g(r^2)
+                a.fx = fmaf(-fs, dx, a.fx);                              // f_i = g (x_i - x_j)
+                a.fy = fmaf(-fs, dy, a.fy);
+                a.fz = fmaf(-fs, dz, a.fz);
+                a.u += fmaf(S.eps4f * sr6, sr6 - 1.0f, -S.ucf);
+                a.w = fmaf(fs, r2, a.w);
+            }
         }
     }
     return a;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ AccD force_f64(const Arrays& A, const Scal& S, const Rep& R,
@@ -128,7 +145,8 @@ __device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[N
 
 // Refresh criterion and step bookkeeping, run by one thread of the CTA that completed the last
 // tile of replica r in this launch.
-__device__ void finish_replica_step(const Arrays& A, const Scal& S, int r)
+__device__ void finish_replica_step(const Arrays& A, const Scal& S, int r, cudaGraphConditionalHandle cond,
+                                    int use_cond)
 {
     RepState& st = A.rs[r];
     st.tiles_done = 0;
@@ -152,16 +170,19 @@ __device__ void finish_replica_step(const Arrays& A, const Scal& S, int r)
         st.rebuild = 1;
         st.reorder = reorder;
         st.max_occ = 0;
-        A.g->any_rebuild = 1;
         if (reorder) A.g->any_reorder = 1;
+        // the first replica to ask for a rebuild in this step opens the graph's IF node (one
+        // caller per step: concurrent cudaGraphSetConditional calls are not allowed)
+        if (atomicExch(&A.g->any_rebuild, 1) == 0 && use_cond) cudaGraphSetConditional(cond, 1u);
     }
 }
 
 // ------------------------------------------------------------------------------------------
 // fused force + leapfrog step
 // ------------------------------------------------------------------------------------------
-template <int MODE, bool PROPS>
-__global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur)
+template <int MODE, bool PROPS, int NB>
+__global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
+                                                 int use_cond)
 {
     __shared__ float sh_max[TILE / 32];
     __shared__ double sh_part[PROPS ? TILE / 32 : 1][NPROP];
@@ -218,7 +239,15 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur)
             } else {
                 const float4* pos = A.pos32[cur];
                 const float4 pi = __ldg(pos + slot);
-                const AccF a = force_f32(A, S, R, pos, slot, pi);
+                if (MODE == MD_MIXED) {
+                    // bring the FP64 state towards L2 while the pair loop runs
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { prefetch_l2(A.v[q] + slot); prefetch_l2(A.xl[q] + slot); }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) prefetch_l2(A.v32[q] + slot);
+                }
+                const AccF a = force_f32<NB>(A, S, R, pos, slot, pi);
                 const float f[3] = {a.fx, a.fy, a.fz};
                 float pn[3];
                 double vn2 = 0.0;
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur)
                     float vf[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
-                        double v = A.v[q][slot];
+                        double v = __ldcs(A.v[q] + slot);
                         const double fq = double(f[q]);
                         if (PROPS) {
                             const double vn = vhalf ? fma(S.c, fq, v) : v;
@@ -235,9 +264,9 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur)
                             part[3 + q] = S.mass * vn;
                         }
                         v = fma(kick, fq, v);
-                        const double x = fma(S.dt, v, A.xl[q][slot]);
-                        A.v[q][slot] = v;
-                        A.xl[q][slot] = x;
+                        const double x = fma(S.dt, v, __ldcs(A.xl[q] + slot));
+                        __stcs(A.v[q] + slot, v);
+                        __stcs(A.xl[q] + slot, x);
                         pn[q] = __double2float_rn(x);
                         vf[q] = __double2float_rn(v);
                     }
@@ -285,7 +314,7 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur)
             sh_last = (atomicAdd(&A.rs[r].tiles_done, 1) == R.ntiles - 1);
             if (sh_last) {
                 __threadfence();
-                finish_replica_step(A, S, r);
+                finish_replica_step(A, S, r, cond, use_cond);
             }
         }
         __syncthreads();
@@ -310,7 +339,7 @@ __global__ void __launch_bounds__(TILE) k_forces(Arrays A, Scal S, int cur)
             A.wvir[slot] = a.w;
         } else {
             const float4 pi = A.pos32[cur][slot];
-            const AccF a = force_f32(A, S, R, A.pos32[cur], slot, pi);
+            const AccF a = force_f32<4>(A, S, R, A.pos32[cur], slot, pi);
             A.f[slot] = make_double4_32a(a.fx, a.fy, a.fz, a.u);
             A.wvir[slot] = a.w;
         }
@@ -526,12 +555,20 @@ static int tile_grid(const Scal& S, const Launch& L)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props)
 {
     const int g = tile_grid(S, L);
-#define GBMD_STEP(M)                                                                     \
-    if (props) k_step<M, true><<<g, TILE, 0, L.stream>>>(A, S, cur);                   \
-    else k_step<M, false><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    if (S.mode == MD_FP64) { GBMD_STEP(MD_FP64) }
-    else if (S.mode == MD_MIXED) { GBMD_STEP(MD_MIXED) }
-    else { GBMD_STEP(MD_FP32) }
+#define GBMD_STEP(M, NB)                                                                             \
+    if (props) k_step<M, true, NB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);        \
+    else k_step<M, false, NB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);
+    if (S.mode == MD_FP64) {
+        GBMD_STEP(MD_FP64, 1)
+    } else if (S.mode == MD_MIXED) {
+        if (L.nbr_batch >= 8) { GBMD_STEP(MD_MIXED, 8) }
+        else if (L.nbr_batch >= 4) { GBMD_STEP(MD_MIXED, 4) }
+        else { GBMD_STEP(MD_MIXED, 2) }
+    } else {
+        if (L.nbr_batch >= 8) { GBMD_STEP(MD_FP32, 8) }
+        else if (L.nbr_batch >= 4) { GBMD_STEP(MD_FP32, 4) }
+        else { GBMD_STEP(MD_FP32, 2) }
+    }
 #undef GBMD_STEP
     if (props) k_props_finalize<<<S.nrep, 256, 0, L.stream>>>(A, S, 1, 1);
     return cudaGetLastError();

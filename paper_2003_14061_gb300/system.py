@@ -180,13 +180,9 @@ class MDSystem:
     def check(self):
         self._call("md_check")
 
-    def set_tuning(self, ctas_per_sm: int = 0, use_graph: int = None):
-        t = B.md_tuning()
-        self._call("md_get_tuning", ctypes.byref(t))
-        if ctas_per_sm:
-            t.ctas_per_sm = int(ctas_per_sm)
-        if use_graph is not None:
-            t.use_graph = int(use_graph)
+    def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0):
+        """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct."""
+        t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph))
         self._call("md_set_tuning", ctypes.byref(t))
 
     def set_timing(self, enable: bool = True):

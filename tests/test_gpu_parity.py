@@ -137,6 +137,20 @@ def test_repeat_runs_bit_identical():
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
+def test_graph_and_direct_launches_agree_bitwise():
+    a, x, v, box, rc, skin = make("lj1372", "mixed")
+    b, *_ = make("lj1372", "mixed")
+    a.set_tuning(use_graph=1)
+    b.set_tuning(use_graph=2)
+    a.integrate(100)                     # 6 graph replays of 16 steps + 4 direct steps
+    b.integrate(100)
+    xa, va, _ = a.state()
+    xb, vb, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    pa, pb = a.props()[0], b.props()[0]
+    assert pa["rebuilds"] == pb["rebuilds"] and pa["step"] == pb["step"] == 100
+
+
 def test_energy_conservation_matches_oracle():
     s, x, v, box, rc, skin = make("wca2048", "mixed", props_every=10)
     s.integrate(1000)
