@@ -152,8 +152,10 @@ def run_gb300(args, rank, world, local_rank):
     n = x.shape[0]
     s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
                  rebuild_rule="vmax", **geo)
-    if args.ctas_per_sm:
-        s.set_tuning(ctas_per_sm=args.ctas_per_sm)
+    if args.ctas_per_sm or args.nbr_batch or args.build_batch:
+        s.set_tuning(ctas_per_sm=args.ctas_per_sm, nbr_batch=args.nbr_batch, build_batch=args.build_batch)
+    if args.no_graph:          # direct launches (ncu cannot profile kernels of graphs with IF nodes)
+        s.set_tuning(use_graph=2)
     stream = s.stream
     # warm-up (also melts the lattice: timed steps see a fluid)
     s.integrate(args.warmup)
@@ -199,7 +201,7 @@ def run_gb300(args, rank, world, local_rank):
     s.integrate(min(args.steps, args.phase_steps))
     phases = s.timing()
     s.set_timing(False)
-    s.set_tuning(use_graph=1)
+    s.set_tuning(use_graph=2 if args.no_graph else 1)
     step_ms, step_calls, step_launches = phases["step"]
     peak, peak_kind = load_peaks()
     bpa = algorithmic_bytes_per_atom_step(mean_nbrs)
@@ -321,6 +323,9 @@ def main():
     ap.add_argument("--workload", default="wca4m", choices=list(WORKLOADS))
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--ncell", type=int, default=0, help="fcc cells per axis (smaller case for profiling)")
+    ap.add_argument("--nbr-batch", type=int, default=0)
+    ap.add_argument("--build-batch", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--phase-steps", type=int, default=400)
     ap.add_argument("--cpu-steps", type=int, default=10)
