@@ -210,6 +210,25 @@ int md_get_timing(md_system* s, double* ms, int64_t* calls, int64_t* launches);
 /* Release the system (host-side bookkeeping and graphs).  The workspace stays the caller's. */
 int md_destroy(md_system* s);
 
+/* Forces for a small system without any device allocation (the paper has no counterpart).
+ * For callers that cannot allocate device memory where they need forces -- code issuing work
+ * while a stream is being captured into a CUDA graph, hosts that only hand out pre-planned
+ * buffers, loops that must not risk the synchronisation of cudaMalloc/cudaFree -- this computes
+ * f_i and u_i as md_compute_forces does (FP32 pair arithmetic on cell-local coordinates), over a
+ * plain cell list of side >= rc (skin is ignored) kept in one file-scope device array of
+ * 1.75 MiB that every GPU loading the library holds until exit.
+ *   p      : eps, sigma, rc, shift_energy and box are used; the rest is ignored.
+ *   n      : 1..65536 atoms; the box may hold at most 65536 cells of side >= rc
+ *            (MD_ERR_INVALID_ARG otherwise, before any work is queued; md_last_error says which).
+ *   x      : device, [n][3] FP64 positions (wrapped into the box on the fly).
+ *   f      : device, [n][3] FP64 output forces;  u: device, [n] FP64 output u_i, or NULL.
+ *   stream : cudaStream_t as void*; the call only queues work and does not wait.
+ * The array is shared by all calls and keeps the last call's contents (each call clears what it
+ * needs to start at zero); calls whose work overlaps on the GPU race on it and must not be
+ * issued.  The first call on each device looks up the array's device address with that device
+ * current, so it should come before any stream capture.  Calls no cudaMalloc or cudaFree. */
+int md_forces_static(const md_params* p, int64_t n, const double* x, double* f, double* u, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* md_last_error(void);
 

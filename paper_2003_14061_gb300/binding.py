@@ -26,7 +26,7 @@ EXPORTS = (
     "md_build_neighbours", "md_compute_forces", "md_integrate", "md_reduce_props", "md_get_series",
     "md_clear_series", "md_get_state", "md_set_state", "md_get_cells", "md_get_neighbours", "md_check",
     "md_nrep", "md_natoms", "md_nbr_capacity", "md_cells_per_axis", "md_set_tuning", "md_get_tuning",
-    "md_destroy", "md_last_error", "md_set_timing", "md_get_timing",
+    "md_destroy", "md_last_error", "md_set_timing", "md_get_timing", "md_forces_static",
 )
 NPHASE = 6
 PHASES = ("step", "bin", "reorder", "build", "props", "other")
@@ -113,6 +113,7 @@ def lib(build_if_missing: bool = True):
             "md_set_timing": (ctypes.c_int, [vp, i32]),
             "md_get_timing": (ctypes.c_int, [vp, vp, vp, vp]),
             "md_last_error": (ctypes.c_char_p, []),
+            "md_forces_static": (ctypes.c_int, [P, i64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -184,6 +184,15 @@ size_t carve(const Plan& P, char* base, Arrays* A)
 
 }  // namespace
 
+namespace gbmd {
+// lets other translation units of the library report through md_last_error
+int set_last_error(int code, const char* msg)
+{
+    g_last_error = msg ? msg : "";
+    return code;
+}
+}  // namespace gbmd
+
 struct md_system {
     struct EvPair {
         cudaEvent_t a, b;

@@ -194,6 +194,9 @@ struct Launch {
     int use_cond;             // 1 while capturing md_integrate into a graph
 };
 
+// records msg for md_last_error() on this thread and returns code (api.cu)
+int set_last_error(int code, const char* msg);
+
 // rebuild path (kernels_rebuild.cu)
 cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder);
 cudaError_t launch_rebuild(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
