@@ -172,6 +172,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.chunk = c.take<int32_t>(size_t(P.nchunks));
     a.tile_rep = c.take<int32_t>(size_t(P.ntiles));
     a.tile_part = c.take<double>(size_t(P.ntiles) * NPROP);
+    a.slice_part = c.take<double>(size_t(P.nrep) * PROPS_SPLIT * NPROP);
     a.rep = c.take<Rep>(size_t(P.nrep));
     a.rs = c.take<RepState>(size_t(P.nrep));
     a.props = c.take<md_props>(size_t(P.nrep));
@@ -310,6 +311,14 @@ void fill_scal(md_system* s)
     S.mass = p.mass;
     S.c = p.dt / (2.0 * p.mass);
     S.half_skin = 0.5 * p.skin;
+    {
+        // |fl(a) - fl(b) - (a - b)| for cell-local coordinates |a|, |b| < 2 (w + skin): two
+        // roundings of the positions plus one of the difference, per axis, summed over 3 axes
+        double wmax = 0.0;
+        for (const Rep& R : P.reps) for (int a = 0; a < 3; ++a) wmax = std::max(wmax, R.w[a]);
+        const double ulp = (P.mode == MD_FP64) ? std::ldexp(1.0, -52) : std::ldexp(1.0, -23);
+        S.disp_margin = 3.0 * 3.0 * ulp * 2.0 * (wmax + p.skin);
+    }
     const double rl = p.rc + p.skin;
     S.rc2d = p.rc * p.rc;
     S.rl2d = rl * rl;
@@ -338,6 +347,9 @@ int apply_tuning(md_system* s)
     s->L.build_block = TILE;
     s->L.nbr_batch = s->tune.nbr_batch;
     s->L.build_batch = s->tune.build_batch;
+    s->L.ctas_req = per_sm;
+    // a persistent grid larger than what can be resident would run as a trailing second wave
+    s->L.grid_step = s->nsm * std::min(per_sm, step_ctas_per_sm(s->S, s->L));
     return MD_OK;
 }
 
@@ -503,7 +515,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
     s->nsm = prop.multiProcessorCount;
     s->tune.ctas_per_sm = 12;
-    s->tune.nbr_batch = 4;
+    s->tune.nbr_batch = 2;
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
     apply_tuning(s);
@@ -599,7 +611,7 @@ int md_integrate(md_system* s, int32_t nsteps)
     for (; k < nsteps; ++k) {
         const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
         {
-            Phase t(s, MD_PHASE_STEP, props ? 2 : 1);
+            Phase t(s, MD_PHASE_STEP, props ? 3 : 1);
             GBMD_CUDA(launch_step(s->A, s->S, s->L, s->cur, props));
         }
         s->cur ^= 1;
@@ -654,7 +666,7 @@ int md_reduce_props(md_system* s, md_props* out)
 {
     if (!s || !out) return fail(MD_ERR_INVALID_ARG, "system or out is NULL");
     {
-        Phase t(s, MD_PHASE_PROPS, 3);
+        Phase t(s, MD_PHASE_PROPS, 4);
         GBMD_CUDA(launch_props(s->A, s->S, s->L, s->cur, true, false));
     }
     GBMD_CUDA(cudaMemcpyAsync(out, s->A.props, sizeof(md_props) * s->plan.nrep, cudaMemcpyDeviceToHost,
@@ -768,8 +780,8 @@ int md_set_tuning(md_system* s, const md_tuning* t)
 {
     if (!s || !t) return fail(MD_ERR_INVALID_ARG, "bad arguments");
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(MD_ERR_INVALID_ARG, "ctas_per_sm in 0..64");
-    if (t->nbr_batch && t->nbr_batch != 2 && t->nbr_batch != 4 && t->nbr_batch != 8)
-        return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 2, 4 or 8");
+    if (t->nbr_batch && t->nbr_batch != 1 && t->nbr_batch != 2 && t->nbr_batch != 4)
+        return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 1, 2 or 4");
     if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4)
         return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2 or 4");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");

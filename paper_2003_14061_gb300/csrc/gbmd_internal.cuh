@@ -12,7 +12,7 @@
 //     and v[3].  MD_FP32 keeps pos (float4) and v32[3] as its master state.
 //   * The neighbour matrix W is row-major, W[m * nslots + slot] (Sec. 2.3: the m-th neighbours of
 //     consecutive atoms are adjacent, so the per-atom loop reads it coalesced).  An entry holds
-//     the neighbour slot in bits 0..25 and (o_x+1) | (o_y+1) << 2 | (o_z+1) << 4 in bits 26..31,
+//     (o_x+1) | (o_y+1) << 2 | (o_z+1) << 4 in bits 0..5 and the neighbour slot in bits 6..31,
 //     o being the periodic offset of the neighbour's cell relative to the atom's cell.
 //   * Cells are numbered globally: replica r's cells are cell0_r + (c_z n_y + c_y) n_x + c_x.
 #pragma once
@@ -27,10 +27,11 @@ namespace gbmd {
 constexpr int TILE = 128;                 // slots per tile
 constexpr int NPROP = 8;                  // U, K, W, px, py, pz, (spare), vmax^2
 constexpr int SERIES_COLS = 9;            // step, U, K, W, P, px, py, pz, vmax
-constexpr uint32_t IDX_MASK = 0x03FFFFFFu;
+constexpr int IDX_SHIFT = 6;              // W entry: slot << 6 | (o_z+1) << 4 | (o_y+1) << 2 | (o_x+1)
 constexpr int64_t MAX_SLOTS = int64_t(1) << 26;
 constexpr int MAX_NC = 1023;
 constexpr int SCAN_CHUNK = 2048;          // cells per block of the prefix sum
+constexpr int PROPS_SPLIT = 32;           // CTAs per replica in the first level of the final sums
 
 enum ErrBits { ERR_NBR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
@@ -103,6 +104,7 @@ struct Arrays {
     // per tile
     int32_t* tile_rep;
     double* tile_part;        // NPROP per tile
+    double* slice_part;       // NPROP per (replica, slice) of the final sums
     // per replica
     Rep* rep;
     RepState* rs;
@@ -127,6 +129,7 @@ struct Scal {
     int32_t shift;
     double dt, mass, c;       // c = dt / (2 m)
     double half_skin;
+    double disp_margin;       // rounding margin of a displacement measured on FP32 positions
     double rc2d, rl2d, sig2d, eps4d, eps48d, ucd;
     float rc2f, rl2f, sig2f, eps4f, eps48f, ucf;
 };
@@ -186,9 +189,11 @@ __device__ __forceinline__ long long warp_sum_ll(long long x)
 struct Launch {
     cudaStream_t stream;
     int grid;                 // persistent CTAs for tile loops
+    int grid_step;            // persistent CTAs of the step kernel (capped at its occupancy)
     int step_block;
     int build_block;
-    int nbr_batch;            // W entries loaded together per thread in the pair loop (2, 4, 8)
+    int nbr_batch;            // W entries loaded together per thread in the pair loop (1, 2, 4)
+    int ctas_req;             // requested resident CTAs/SM (register bound of the step kernel)
     int build_batch;          // candidates loaded together per thread in the build (1, 2, 4)
     cudaGraphConditionalHandle cond;   // IF node of the rebuild (inside a captured graph)
     int use_cond;             // 1 while capturing md_integrate into a graph
@@ -207,6 +212,7 @@ cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, i
 
 // step path (kernels_step.cu)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props);
+int step_ctas_per_sm(const Scal& S, const Launch& L);     // resident CTAs/SM of the chosen k_step
 cudaError_t launch_forces(const Arrays& A, const Scal& S, const Launch& L, int cur);
 cudaError_t launch_props(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_forces,
                          bool to_series);

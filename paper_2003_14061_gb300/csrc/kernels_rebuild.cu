@@ -22,14 +22,48 @@
 namespace gbmd {
 
 // ------------------------------------------------------------------------------------------
+// Per-replica statistics (N3: max occupancy; neighbour counts) are accumulated per thread over a
+// CTA's contiguous run of tiles and folded in once per replica: one block reduction and one
+// atomic, instead of an atomic per warp on the same address.  All threads of the CTA call this.
+// ------------------------------------------------------------------------------------------
+__device__ void flush_stats(int64_t* sum_dst, int* max_dst, long long sum, int mx)
+{
+    __shared__ long long sh_sum[TILE / 32];
+    __shared__ int sh_max[TILE / 32];
+    sum = warp_sum_ll(sum);
+    mx = warp_max_i(mx);
+    if ((threadIdx.x & 31) == 0) {
+        sh_sum[threadIdx.x >> 5] = sum;
+        sh_max[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        int m = 0;
+        for (int w = 0; w < TILE / 32; ++w) { tot += sh_sum[w]; m = max(m, sh_max[w]); }
+        if (sum_dst && tot) atomicAdd(reinterpret_cast<unsigned long long*>(sum_dst), static_cast<unsigned long long>(tot));
+        if (max_dst && m > 0) atomicMax(max_dst, m);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
 // N1 + N2
 // ------------------------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int from_set)
 {
     if (!A.g->any_rebuild) return;
-    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(S.ntiles, t_begin + per);
+    int run_r = -1, run_occ = 0;
+    for (int t = t_begin; t < t_end; ++t) {
         const int r = A.tile_rep[t];
+        if (r != run_r) {
+            if (run_r >= 0) flush_stats(nullptr, &A.rs[run_r].max_occ, 0, run_occ);
+            run_r = r;
+            run_occ = 0;
+        }
         if (!A.rs[r].rebuild) continue;
         const Rep& R = A.rep[r];
         if (t == R.tile0 && threadIdx.x == 0) {
@@ -39,6 +73,7 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         const int64_t j = slot - R.slot0;
         int occ = 0;
+        int cell_bin = -1;            // this lane's cell, -1 for padding slots
         if (j < R.n && from_set) {
             // exact binning of a global position (the definition the oracle follows):
             // wrap into [0, L), c = floor(x n_c / L) clamped, local = x - c w, all in FP64
@@ -67,9 +102,7 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
             }
             const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
             A.cell[slot] = cell;
-            const int l = atomicAdd(&A.ccount[cell], 1);
-            A.layer[slot] = l;
-            occ = l + 1;
+            cell_bin = cell;
         } else if (j < R.n) {
             // during a run every atom is within skin/2 < w of its cell: it stays or moves to the
             // adjacent cell along each axis; its local coordinate shifts by -s w (s in -1, 0, 1)
@@ -129,13 +162,26 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
             }
             const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
             if (moved) A.cell[slot] = cell;
-            const int l = atomicAdd(&A.ccount[cell], 1);
-            A.layer[slot] = l;
-            occ = l + 1;
+            cell_bin = cell;
         }
-        occ = warp_max_i(occ);
-        if ((threadIdx.x & 31) == 0 && occ > 0) atomicMax(&A.rs[r].max_occ, occ);
+        // N2 layer slots: lanes of a warp that share a cell (common, the atoms are cell-sorted)
+        // take consecutive layers from one atomic on the cell's counter
+        {
+            const unsigned peers = __match_any_sync(0xffffffffu, cell_bin);
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(peers) - 1;
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            int base = 0;
+            if (cell_bin >= 0 && lane == leader) base = atomicAdd(&A.ccount[cell_bin], __popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (cell_bin >= 0) {
+                A.layer[slot] = base + rank;
+                occ = base + rank + 1;
+            }
+        }
+        run_occ = max(run_occ, occ);
     }
+    if (run_r >= 0) flush_stats(nullptr, &A.rs[run_r].max_occ, 0, run_occ);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -353,8 +399,18 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
     if constexpr (sizeof(T) == 8) pos = reinterpret_cast<const P4*>(A.pos64[cur]);
     else pos = reinterpret_cast<const P4*>(A.pos32[cur]);
     const T rl2 = (sizeof(T) == 8) ? T(S.rl2d) : T(S.rl2f);
-    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(S.ntiles, t_begin + per);
+    int run_r = -1, run_max = 0;
+    long long run_sum = 0;
+    for (int t = t_begin; t < t_end; ++t) {
         const int r = A.tile_rep[t];
+        if (r != run_r) {
+            if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
+            run_r = r;
+            run_sum = 0;
+            run_max = 0;
+        }
         if (!A.rs[r].rebuild) continue;
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
@@ -369,6 +425,7 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
             else { w[0] = R.wf[0]; w[1] = R.wf[1]; w[2] = R.wf[2]; }
             const int xm = (cx == 0) ? R.nc[0] - 1 : cx - 1;
             const int xp = (cx == R.nc[0] - 1) ? 0 : cx + 1;
+            uint32_t* wp = A.W + slot;         // next free entry of this atom's column of W
             for (int oz = -1; oz <= 1; ++oz) {
                 int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
                 const T offz = T(oz) * w[2];
@@ -376,12 +433,41 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
                     int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
                     const T offy = T(oy) * w[1];
                     const int row = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0];
-                    // the three cells of this row, as [b0,e0) [b1,e1) [b2,e2) in perm
+                    const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
+                    // the three cells of this row, as [b0,e0) [b1,e1) [b2,e2) in perm; without a
+                    // periodic wrap in x they are one contiguous range [b0, e2) split at b1, b2
                     const int b0 = A.cstart[row + xm], e0 = A.cstart[row + xm + 1];
                     const int b1 = A.cstart[row + cx], e1 = A.cstart[row + cx + 1];
                     const int b2 = A.cstart[row + xp], e2 = A.cstart[row + xp + 1];
+                    if (cx > 0 && cx < R.nc[0] - 1) {
+                        for (int k0 = b0; k0 < e2; k0 += BB) {
+                            int32_t js[BB];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) js[u] = A.perm[min(k0 + u, e2 - 1)];
+                            P4 pj[BB];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) pj[u] = pos[js[u]];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) {
+                                const int k = k0 + u;
+                                const int ox = int(k >= b1) + int(k >= b2) - 1;
+                                const T offx = (ox < 0) ? -w[0] : ((ox > 0) ? w[0] : T(0));
+                                const T dx = add_rn(sub_rn(pj[u].x, pi.x), offx);
+                                const T dy = add_rn(sub_rn(pj[u].y, pi.y), offy);
+                                const T dz = add_rn(sub_rn(pj[u].z, pi.z), offz);
+                                const T r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
+                                if (k < e2 && r2 < rl2 && js[u] != slot) {
+                                    if (m < S.cap) {
+                                        *wp = (uint32_t(js[u]) << IDX_SHIFT) | codeyz | uint32_t(ox + 1);
+                                        wp += S.nslots;
+                                    }
+                                    ++m;
+                                }
+                            }
+                        }
+                        continue;
+                    }
                     const int n0 = e0 - b0, n01 = n0 + (e1 - b1), ntot = n01 + (e2 - b2);
-                    const uint32_t codeyz = ((uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4)) << 26;
                     for (int q0 = 0; q0 < ntot; q0 += BB) {
                         int32_t js[BB];
 #pragma unroll
@@ -404,8 +490,10 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
                             const T dz = add_rn(sub_rn(pj[u].z, pi.z), offz);
                             const T r2 = fma_rn(dz, dz, fma_rn(dy, dy, mul_rn(dx, dx)));
                             if (r2 < rl2) {
-                                if (m < S.cap)
-                                    A.W[int64_t(m) * S.nslots + slot] = uint32_t(js[u]) | codeyz | (uint32_t(ox + 1) << 26);
+                                if (m < S.cap) {
+                                    *wp = (uint32_t(js[u]) << IDX_SHIFT) | codeyz | uint32_t(ox + 1);
+                                    wp += S.nslots;
+                                }
                                 ++m;
                             }
                         }
@@ -421,14 +509,12 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
                 atomicMax(&A.g->max_nbr_seen, m);
             }
         }
-        const long long sum = warp_sum_ll(active ? m : 0);
-        const int mx = warp_max_i(m);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(reinterpret_cast<unsigned long long*>(&A.rs[r].sum_nbrs),
-                      static_cast<unsigned long long>(sum));
-            atomicMax(&A.rs[r].max_nbrs, mx);
+        if (active) {
+            run_sum += m;
+            run_max = max(run_max, m);
         }
     }
+    if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -19,10 +19,19 @@
 
 namespace gbmd {
 
-// offset code (0, 1, 2) of one axis -> (code - 1) as an exact float, without a conversion op
-__device__ __forceinline__ float offset_f(uint32_t code2)
+// Periodic offsets of a W entry as exact floats without conversion ops: OR-ing the code bits into
+// the mantissa of 2^23 gives 2^23 + code; subtracting 2^23 + (the code of offset 0) leaves
+// o_x, 4 o_y and 16 o_z, which multiply w_x, w_y / 4 and w_z / 16 (exact power-of-two scalings).
+__device__ __forceinline__ float offx_f(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 3u)) - 8388609.0f; }
+__device__ __forceinline__ float offy4_f(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 12u)) - 8388612.0f; }
+__device__ __forceinline__ float offz16_f(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 48u)) - 8388624.0f; }
+
+// reciprocal to ~1 ulp (the force tolerance is 1e-5 relative)
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    return __uint_as_float(0x4B000000u | code2) - 8388609.0f;
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -40,7 +49,7 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
     AccF a{0.f, 0.f, 0.f, 0.f, 0.f};
     const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
     const uint32_t* __restrict__ Wc = A.W + slot;
-    const float wx = R.wf[0], wy = R.wf[1], wz = R.wf[2];
+    const float wx = R.wf[0], wy4 = 0.25f * R.wf[1], wz16 = 0.0625f * R.wf[2];
     for (int m0 = 0; m0 < mm; m0 += NB) {
         uint32_t e[NB];
 #pragma unroll
@@ -49,16 +58,16 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
         float4 pj[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k)
-            pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] & IDX_MASK)) : pi;
+            pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] >> IDX_SHIFT)) : pi;
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const uint32_t ek = e[k];
-            const float dx = fmaf(offset_f((ek >> 26) & 3u), wx, pj[k].x - pi.x);
-            const float dy = fmaf(offset_f((ek >> 28) & 3u), wy, pj[k].y - pi.y);
-            const float dz = fmaf(offset_f(ek >> 30), wz, pj[k].z - pi.z);
+            const float dx = fmaf(offx_f(ek), wx, pj[k].x - pi.x);
+            const float dy = fmaf(offy4_f(ek), wy4, pj[k].y - pi.y);
+            const float dz = fmaf(offz16_f(ek), wz16, pj[k].z - pi.z);
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             if (m0 + k < mm && r2 < S.rc2f) {
-                const float ri2 = __frcp_rn(r2);
+                const float ri2 = rcp_approx(r2);
                 const float sr2 = S.sig2f * ri2;
                 const float sr6 = sr2 * sr2 * sr2;
                 const float fs = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;   // g(r^2)
@@ -86,10 +95,10 @@ __device__ __forceinline__ AccD force_f64(const Arrays& A, const Scal& S, const 
     const uint32_t* __restrict__ Wc = A.W + slot;
     for (int m = 0; m < mm; ++m) {
         const uint32_t e = Wc[int64_t(m) * S.nslots];
-        const double4_32a pj = pos[e & IDX_MASK];
-        const double dx = fma(double(int((e >> 26) & 3u) - 1), R.w[0], pj.x - pi.x);
-        const double dy = fma(double(int((e >> 28) & 3u) - 1), R.w[1], pj.y - pi.y);
-        const double dz = fma(double(int(e >> 30) - 1), R.w[2], pj.z - pi.z);
+        const double4_32a pj = pos[e >> IDX_SHIFT];
+        const double dx = fma(double(int(e & 3u) - 1), R.w[0], pj.x - pi.x);
+        const double dy = fma(double(int((e >> 2) & 3u) - 1), R.w[1], pj.y - pi.y);
+        const double dz = fma(double(int((e >> 4) & 3u) - 1), R.w[2], pj.z - pi.z);
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         if (r2 < S.rc2d) {
             const double ri2 = 1.0 / r2;
@@ -120,26 +129,40 @@ __device__ __forceinline__ float tile_max(float v, float* sh)
     return m;
 }
 
+// Per-tile FP64 sums of the 7 additive quantities and the FP32 maximum of |v|^2.  The 8 doubles
+// of each lane are reduced across the warp by reduce-scatter (each exchange halves the number of
+// quantities a lane carries, 4 + 2 + 1 adds, then 2 more over the last 4 lanes): 9 FP64 adds per
+// lane instead of 35 for a butterfly per quantity (FP64 runs at 1/72 of the FP32 rate on GB300).
 __device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[NPROP], double* out)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float vm = warp_max(float(p[NPROP - 1]));
+    p[NPROP - 1] = 0.0;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    double a4[4];
 #pragma unroll
-    for (int q = 0; q < NPROP - 1; ++q) p[q] = warp_sum(p[q]);
-    {
-        double x = p[NPROP - 1];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        p[NPROP - 1] = x;
+    for (int k = 0; k < 4; ++k) {
+        const double keep = h16 ? p[4 + k] : p[k], give = h16 ? p[k] : p[4 + k];
+        a4[k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
     }
-    if ((threadIdx.x & 31) == 0) {
+    double a2[2];
 #pragma unroll
-        for (int q = 0; q < NPROP; ++q) sh[threadIdx.x >> 5][q] = p[q];
+    for (int k = 0; k < 2; ++k) {
+        const double keep = h8 ? a4[2 + k] : a4[k], give = h8 ? a4[k] : a4[2 + k];
+        a2[k] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
     }
+    double a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+    const int q = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+    if ((lane & 3) == 0 && q != NPROP - 1) sh[warp][q] = a1;
+    if (lane == 0) sh[warp][NPROP - 1] = double(vm);
     __syncthreads();
     if (threadIdx.x < NPROP) {
-        const int q = threadIdx.x;
-        double s = sh[0][q];
-        for (int k = 1; k < TILE / 32; ++k) s = (q == NPROP - 1) ? fmax(s, sh[k][q]) : s + sh[k][q];
-        out[q] = s;
+        const int k = threadIdx.x;
+        double s = sh[0][k];
+        for (int w = 1; w < TILE / 32; ++w) s = (k == NPROP - 1) ? fmax(s, sh[w][k]) : s + sh[w][k];
+        out[k] = s;
     }
 }
 
@@ -156,9 +179,10 @@ __device__ void finish_replica_step(const Arrays& A, const Scal& S, int r, cudaG
     st.vhalf = 1;
     bool rebuild;
     if (S.rule == MD_REBUILD_VMAX) {
-        // D bounds every atom's displacement since the last rebuild (triangle inequality);
-        // the factor covers the FP32 rounding of |v|.
-        st.D += S.dt * sqrt(double(m2)) * (1.0 + 1e-6);
+        // D bounds every atom's displacement since the last rebuild (triangle inequality):
+        // max_i |x_{n+1} - x_n| = dt max_i |v_{n+1/2}|, measured on the FP32 position copies,
+        // plus a margin covering their rounding
+        st.D += sqrt(double(m2)) * (1.0 + 1e-6) + S.disp_margin;
         rebuild = st.D > S.half_skin;
     } else if (S.rule == MD_REBUILD_DISP) {
         rebuild = sqrt(double(m2)) * (1.0 + 1e-6) > S.half_skin;
@@ -177,18 +201,73 @@ __device__ void finish_replica_step(const Arrays& A, const Scal& S, int r, cudaG
     }
 }
 
+// Fold one CTA's contribution to replica r: the maximum of the refresh metric over its tiles
+// and the number of tiles it completed.  The CTA that brings the count to the replica's tile
+// total runs the refresh bookkeeping (the last-block pattern).  All threads of the CTA call this.
+__device__ __forceinline__ void flush_replica(const Arrays& A, const Scal& S, int r, float run_max, int tiles,
+                                              float* sh, cudaGraphConditionalHandle cond, int use_cond)
+{
+    const float m = tile_max(run_max, sh);
+    if (threadIdx.x == 0) {
+        atomicMax(&A.rs[r].vmax2, __float_as_uint(m));
+        __threadfence();
+        const int done = atomicAdd(&A.rs[r].tiles_done, tiles) + tiles;
+        if (done == A.rep[r].ntiles) {
+            __threadfence();
+            finish_replica_step(A, S, r, cond, use_cond);
+        }
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------------------------------------
 // fused force + leapfrog step
 // ------------------------------------------------------------------------------------------
-template <int MODE, bool PROPS, int NB>
-__global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
+template <int MODE, bool PROPS, int NB, int MINB>
+__global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                  int use_cond)
 {
     __shared__ float sh_max[TILE / 32];
     __shared__ double sh_part[PROPS ? TILE / 32 : 1][NPROP];
-    __shared__ int sh_last;
     const int nxt = cur ^ 1;
-    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    // Each CTA takes a contiguous run of tiles.  Software pipeline over them: while tile t is
+    // computed, tile t+1's state and the rows of W below each atom's count are prefetched into
+    // L2 (the counts are read one tile earlier still), so the next tile's HBM traffic is in
+    // flight without holding registers.
+    const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per;
+    const int t_end = min(S.ntiles, t_begin + per);
+    int c_ahead = 0;
+    if (MODE != MD_FP64 && t_begin + 1 < t_end)
+        c_ahead = __ldcs(A.nbr_count + int64_t(t_begin + 1) * TILE + threadIdx.x);
+    // the refresh metric is kept per thread across this CTA's tiles of one replica and folded
+    // into the replica's counters once per replica (one fence per CTA, not per tile)
+    int run_r = -1, run_tiles = 0;
+    float run_max = 0.0f;
+    for (int t = t_begin; t < t_end; ++t) {
+        if (MODE != MD_FP64) {
+            if (t + 1 < t_end) {
+                const int64_t s1 = int64_t(t + 1) * TILE + threadIdx.x;
+                prefetch_l2(A.pos32[cur] + s1);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (MODE == MD_MIXED) { prefetch_l2(A.xl[q] + s1); prefetch_l2(A.v[q] + s1); }
+                    else prefetch_l2(A.v32[q] + s1);
+                }
+                const int mm1 = min(c_ahead, S.cap);
+                for (int m = 0; m < mm1; ++m) prefetch_l2(A.W + int64_t(m) * S.nslots + s1);
+            }
+            c_ahead = (t + 2 < t_end) ? __ldcs(A.nbr_count + int64_t(t + 2) * TILE + threadIdx.x) : 0;
+        }
+        {
+            const int r_t = A.tile_rep[t];
+            if (r_t != run_r) {
+                if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+                run_r = r_t;
+                run_tiles = 0;
+                run_max = 0.0f;
+            }
+        }
         const int r = A.tile_rep[t];
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
@@ -206,20 +285,19 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGr
                 const double f[3] = {a.fx, a.fy, a.fz};
                 double xl[3] = {pi.x, pi.y, pi.z};
                 const double kick = vhalf ? 2.0 * S.c : S.c;
-                double vn2 = 0.0, vv[3];
+                double vn2 = 0.0;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     double v = A.v[q][slot];
                     if (PROPS) {
                         const double vn = vhalf ? fma(S.c, f[q], v) : v;
                         vn2 = fma(vn, vn, vn2);
-                        part[3 + q] = S.mass * vn;
+                        part[3 + q] = vn;
                     }
                     v = fma(kick, f[q], v);
                     xl[q] = fma(S.dt, v, xl[q]);
                     A.v[q][slot] = v;
                     A.xl[q][slot] = xl[q];
-                    vv[q] = v;
                 }
                 A.pos64[nxt][slot] = make_double4_32a(xl[0], xl[1], xl[2], pi.w);
                 if (S.rule == MD_REBUILD_DISP) {
@@ -228,24 +306,26 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGr
                                 d2 = float(xl[2] - double(xr.z));
                     metric = d0 * d0 + d1 * d1 + d2 * d2;
                 } else {
-                    metric = float(vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2]);
+                    const double d0 = xl[0] - pi.x, d1 = xl[1] - pi.y, d2 = xl[2] - pi.z;
+                    metric = float(d0 * d0 + d1 * d1 + d2 * d2);
                 }
                 if (PROPS) {
-                    part[0] = 0.5 * a.u;
-                    part[1] = 0.5 * S.mass * vn2;
-                    part[2] = 0.5 * a.w;
+                    part[0] = a.u;
+                    part[1] = vn2;
+                    part[2] = a.w;
                     part[NPROP - 1] = vn2;
                 }
             } else {
                 const float4* pos = A.pos32[cur];
                 const float4 pi = __ldg(pos + slot);
-                if (MODE == MD_MIXED) {
-                    // bring the FP64 state towards L2 while the pair loop runs
+                if (t == t_begin) {                      // first tile of this CTA: nothing prefetched yet
+                    if (MODE == MD_MIXED) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) { prefetch_l2(A.v[q] + slot); prefetch_l2(A.xl[q] + slot); }
-                } else {
+                        for (int q = 0; q < 3; ++q) { prefetch_l2(A.v[q] + slot); prefetch_l2(A.xl[q] + slot); }
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) prefetch_l2(A.v32[q] + slot);
+                        for (int q = 0; q < 3; ++q) prefetch_l2(A.v32[q] + slot);
+                    }
                 }
                 const AccF a = force_f32<NB>(A, S, R, pos, slot, pi);
                 const float f[3] = {a.fx, a.fy, a.fz};
@@ -253,7 +333,6 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGr
                 double vn2 = 0.0;
                 if (MODE == MD_MIXED) {
                     const double kick = vhalf ? 2.0 * S.c : S.c;
-                    float vf[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         double v = __ldcs(A.v[q] + slot);
@@ -261,35 +340,40 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGr
                         if (PROPS) {
                             const double vn = vhalf ? fma(S.c, fq, v) : v;
                             vn2 = fma(vn, vn, vn2);
-                            part[3 + q] = S.mass * vn;
+                            part[3 + q] = vn;
                         }
                         v = fma(kick, fq, v);
                         const double x = fma(S.dt, v, __ldcs(A.xl[q] + slot));
                         __stcs(A.v[q] + slot, v);
                         __stcs(A.xl[q] + slot, x);
                         pn[q] = __double2float_rn(x);
-                        vf[q] = __double2float_rn(v);
                     }
-                    if (S.rule != MD_REBUILD_DISP) metric = fmaf(vf[2], vf[2], fmaf(vf[1], vf[1], vf[0] * vf[0]));
+                    // |x_{n+1} - x_n| = dt |v_{n+1/2}| from the FP32 copies of both positions
+                    // (same cell frame); the per-step rounding margin is added in the finish
+                    if (S.rule != MD_REBUILD_DISP) {
+                        const float d0 = pn[0] - pi.x, d1 = pn[1] - pi.y, d2 = pn[2] - pi.z;
+                        metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                    }
                 } else {
                     const float kick = float(vhalf ? 2.0 * S.c : S.c);
                     const float cf = float(S.c), dtf = float(S.dt);
                     const float pc[3] = {pi.x, pi.y, pi.z};
-                    float vf[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         float v = A.v32[q][slot];
                         if (PROPS) {
                             const float vn = vhalf ? fmaf(cf, f[q], v) : v;
                             vn2 = fma(double(vn), double(vn), vn2);
-                            part[3 + q] = S.mass * double(vn);
+                            part[3 + q] = double(vn);
                         }
                         v = fmaf(kick, f[q], v);
                         A.v32[q][slot] = v;
                         pn[q] = fmaf(dtf, v, pc[q]);
-                        vf[q] = v;
                     }
-                    if (S.rule != MD_REBUILD_DISP) metric = fmaf(vf[2], vf[2], fmaf(vf[1], vf[1], vf[0] * vf[0]));
+                    if (S.rule != MD_REBUILD_DISP) {
+                        const float d0 = pn[0] - pi.x, d1 = pn[1] - pi.y, d2 = pn[2] - pi.z;
+                        metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                    }
                 }
                 A.pos32[nxt][slot] = make_float4(pn[0], pn[1], pn[2], pi.w);
                 if (S.rule == MD_REBUILD_DISP) {
@@ -298,27 +382,22 @@ __global__ void __launch_bounds__(TILE) k_step(Arrays A, Scal S, int cur, cudaGr
                     metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
                 }
                 if (PROPS) {
-                    part[0] = 0.5 * double(a.u);
-                    part[1] = 0.5 * S.mass * vn2;
-                    part[2] = 0.5 * double(a.w);
+                    part[0] = double(a.u);
+                    part[1] = vn2;
+                    part[2] = double(a.w);
                     part[NPROP - 1] = vn2;
                 }
             }
             if (!(metric <= 3.0e38f)) metric = __uint_as_float(0x7f800000u);   // +inf marks non-finite
         }
-        const float tmax = tile_max(metric, sh_max);
-        if (PROPS) tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
-        if (threadIdx.x == 0) {
-            atomicMax(&A.rs[r].vmax2, __float_as_uint(tmax));
-            __threadfence();
-            sh_last = (atomicAdd(&A.rs[r].tiles_done, 1) == R.ntiles - 1);
-            if (sh_last) {
-                __threadfence();
-                finish_replica_step(A, S, r, cond, use_cond);
-            }
+        run_max = fmaxf(run_max, metric);
+        run_tiles += 1;
+        if (PROPS) {
+            tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
+            __syncthreads();
         }
-        __syncthreads();
     }
+    if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -369,11 +448,11 @@ __global__ void __launch_bounds__(TILE) k_props_tiles(Arrays A, Scal S)
                 if (MODE == MD_FP32) vn = vhalf ? double(fmaf(float(S.c), float(fq[q]), float(v))) : v;
                 else vn = vhalf ? fma(S.c, fq[q], v) : v;
                 vn2 = fma(vn, vn, vn2);
-                part[3 + q] = S.mass * vn;
+                part[3 + q] = vn;
             }
-            part[0] = 0.5 * f.w;
-            part[1] = 0.5 * S.mass * vn2;
-            part[2] = 0.5 * A.wvir[slot];
+            part[0] = f.w;
+            part[1] = vn2;
+            part[2] = A.wvir[slot];
             part[NPROP - 1] = vn2;
         }
         tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
@@ -381,16 +460,20 @@ __global__ void __launch_bounds__(TILE) k_props_tiles(Arrays A, Scal S)
     }
 }
 
-// one CTA per replica: fixed-order sum of its tile partials
-__global__ void __launch_bounds__(256) k_props_finalize(Arrays A, Scal S, int to_series, int step_lag)
+// Final sums, two fixed-order levels: PROPS_SPLIT CTAs per replica each add a contiguous slice
+// of the replica's tile partials, then one warp per replica adds the slices and applies the
+// constant factors (U = sum u_i / 2, K = m sum v^2 / 2, W = sum w_i / 2, P = m sum v).
+__global__ void __launch_bounds__(256) k_props_slices(Arrays A, Scal S)
 {
     __shared__ double sh[256][NPROP];
-    const int r = blockIdx.x;
+    const int r = blockIdx.x / PROPS_SPLIT, b = blockIdx.x % PROPS_SPLIT;
     const Rep& R = A.rep[r];
+    const int per = (R.ntiles + PROPS_SPLIT - 1) / PROPS_SPLIT;
+    const int k0 = b * per, k1 = min(R.ntiles, k0 + per);
     double acc[NPROP];
 #pragma unroll
     for (int q = 0; q < NPROP; ++q) acc[q] = 0.0;
-    for (int k = threadIdx.x; k < R.ntiles; k += blockDim.x) {
+    for (int k = k0 + int(threadIdx.x); k < k1; k += blockDim.x) {
         const double* p = A.tile_part + int64_t(R.tile0 + k) * NPROP;
 #pragma unroll
         for (int q = 0; q < NPROP - 1; ++q) acc[q] += p[q];
@@ -407,33 +490,48 @@ __global__ void __launch_bounds__(256) k_props_finalize(Arrays A, Scal S, int to
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const RepState& st = A.rs[r];
-        const double U = sh[0][0], K = sh[0][1], W = sh[0][2];
-        const double V = R.L[0] * R.L[1] * R.L[2];
-        md_props pr;
-        pr.U = U;
-        pr.K = K;
-        pr.E_per_atom = (U + K) / double(R.n);
-        pr.virial = W;
-        pr.pressure = (2.0 * K + W) / (3.0 * V);
-        pr.P[0] = sh[0][3]; pr.P[1] = sh[0][4]; pr.P[2] = sh[0][5];
-        pr.vmax = sqrt(sh[0][NPROP - 1]);
-        pr.mean_nbrs = double(st.sum_nbrs) / double(R.n);
-        pr.step = st.step - step_lag;
-        pr.rebuilds = st.rebuilds;
-        pr.max_cell_occ = st.max_occ;
-        pr.max_nbrs = st.max_nbrs;
-        A.props[r] = pr;
-        if (to_series) {
-            RepState& sw = A.rs[r];
-            const int row = sw.series_rows;
-            if (row < S.series_cap) {
-                double* o = A.series + (int64_t(r) * S.series_cap + row) * SERIES_COLS;
-                o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
-                o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
-                sw.series_rows = row + 1;
-            }
+    if (threadIdx.x < NPROP) A.slice_part[int64_t(blockIdx.x) * NPROP + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+__global__ void __launch_bounds__(32) k_props_finalize(Arrays A, Scal S, int to_series, int step_lag)
+{
+    const int r = blockIdx.x;
+    const Rep& R = A.rep[r];
+    if (threadIdx.x != 0) return;
+    double acc[NPROP];
+#pragma unroll
+    for (int q = 0; q < NPROP; ++q) acc[q] = 0.0;
+    for (int b = 0; b < PROPS_SPLIT; ++b) {
+        const double* p = A.slice_part + (int64_t(r) * PROPS_SPLIT + b) * NPROP;
+#pragma unroll
+        for (int q = 0; q < NPROP - 1; ++q) acc[q] += p[q];
+        acc[NPROP - 1] = fmax(acc[NPROP - 1], p[NPROP - 1]);
+    }
+    const RepState& st = A.rs[r];
+    const double U = 0.5 * acc[0], K = 0.5 * S.mass * acc[1], W = 0.5 * acc[2];
+    const double V = R.L[0] * R.L[1] * R.L[2];
+    md_props pr;
+    pr.U = U;
+    pr.K = K;
+    pr.E_per_atom = (U + K) / double(R.n);
+    pr.virial = W;
+    pr.pressure = (2.0 * K + W) / (3.0 * V);
+    pr.P[0] = S.mass * acc[3]; pr.P[1] = S.mass * acc[4]; pr.P[2] = S.mass * acc[5];
+    pr.vmax = sqrt(acc[NPROP - 1]);
+    pr.mean_nbrs = double(st.sum_nbrs) / double(R.n);
+    pr.step = st.step - step_lag;
+    pr.rebuilds = st.rebuilds;
+    pr.max_cell_occ = st.max_occ;
+    pr.max_nbrs = st.max_nbrs;
+    A.props[r] = pr;
+    if (to_series) {
+        RepState& sw = A.rs[r];
+        const int row = sw.series_rows;
+        if (row < S.series_cap) {
+            double* o = A.series + (int64_t(r) * S.series_cap + row) * SERIES_COLS;
+            o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
+            o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
+            sw.series_rows = row + 1;
         }
     }
 }
@@ -539,7 +637,7 @@ __global__ void __launch_bounds__(TILE) k_get_nbrs(Arrays A, Scal S, int32_t* co
         const int mm = min(min(m, S.cap), cap_out);
         for (int k = 0; k < mm; ++k) {
             const uint32_t e = A.W[int64_t(k) * S.nslots + slot];
-            nbrs[(id - id_lo) * cap_out + k] = A.id[e & IDX_MASK];
+            nbrs[(id - id_lo) * cap_out + k] = A.id[e >> IDX_SHIFT];
         }
     }
 }
@@ -552,25 +650,61 @@ static int tile_grid(const Scal& S, const Launch& L)
     return std::max(1, std::min(L.grid, S.ntiles));
 }
 
+template <int M, int NB, int MINB>
+static int occ_of()
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<M, false, NB, MINB>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<M, true, NB, MINB>, TILE, 0);
+    return std::max(1, std::min(a, b));
+}
+
+// register bound from the requested residency: __launch_bounds__(TILE, MINB)
+static int minb_of(int ctas_per_sm)
+{
+    return ctas_per_sm >= 16 ? 16 : ctas_per_sm >= 12 ? 12 : ctas_per_sm >= 8 ? 8 : 4;
+}
+
+#define GBMD_DISPATCH_NB_MINB(M, FN)                                                      \
+    {                                                                                     \
+        const int mb = minb_of(L.ctas_req);                                               \
+        const int nb = L.nbr_batch >= 4 ? 4 : L.nbr_batch >= 2 ? 2 : 1;                    \
+        if (nb == 4) {                                                                    \
+            if (mb == 16) FN(M, 4, 16) else if (mb == 12) FN(M, 4, 12) else if (mb == 8) FN(M, 4, 8) else FN(M, 4, 4) \
+        } else if (nb == 2) {                                                             \
+            if (mb == 16) FN(M, 2, 16) else if (mb == 12) FN(M, 2, 12) else if (mb == 8) FN(M, 2, 8) else FN(M, 2, 4) \
+        } else {                                                                          \
+            if (mb == 16) FN(M, 1, 16) else if (mb == 12) FN(M, 1, 12) else if (mb == 8) FN(M, 1, 8) else FN(M, 1, 4) \
+        }                                                                                 \
+    }
+
+int step_ctas_per_sm(const Scal& S, const Launch& L)
+{
+    int occ = 1;
+#define GBMD_OCC(M, NB, MB) { occ = occ_of<M, NB, MB>(); }
+    if (S.mode == MD_FP64) occ = occ_of<MD_FP64, 1, 4>();
+    else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_OCC)
+    else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_OCC)
+#undef GBMD_OCC
+    return occ;
+}
+
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props)
 {
-    const int g = tile_grid(S, L);
-#define GBMD_STEP(M, NB)                                                                             \
-    if (props) k_step<M, true, NB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);        \
-    else k_step<M, false, NB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);
-    if (S.mode == MD_FP64) {
-        GBMD_STEP(MD_FP64, 1)
-    } else if (S.mode == MD_MIXED) {
-        if (L.nbr_batch >= 8) { GBMD_STEP(MD_MIXED, 8) }
-        else if (L.nbr_batch >= 4) { GBMD_STEP(MD_MIXED, 4) }
-        else { GBMD_STEP(MD_MIXED, 2) }
-    } else {
-        if (L.nbr_batch >= 8) { GBMD_STEP(MD_FP32, 8) }
-        else if (L.nbr_batch >= 4) { GBMD_STEP(MD_FP32, 4) }
-        else { GBMD_STEP(MD_FP32, 2) }
+    const int g = std::max(1, std::min(L.grid_step, S.ntiles));
+#define GBMD_STEP(M, NB, MB)                                                                           \
+    {                                                                                                  \
+        if (props) k_step<M, true, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);  \
+        else k_step<M, false, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);       \
     }
+    if (S.mode == MD_FP64) GBMD_STEP(MD_FP64, 1, 4)
+    else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
+    else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)
 #undef GBMD_STEP
-    if (props) k_props_finalize<<<S.nrep, 256, 0, L.stream>>>(A, S, 1, 1);
+    if (props) {
+        k_props_slices<<<S.nrep * PROPS_SPLIT, 256, 0, L.stream>>>(A, S);
+        k_props_finalize<<<S.nrep, 32, 0, L.stream>>>(A, S, 1, 1);
+    }
     return cudaGetLastError();
 }
 
@@ -593,7 +727,8 @@ cudaError_t launch_props(const Arrays& A, const Scal& S, const Launch& L, int cu
     if (S.mode == MD_FP64) k_props_tiles<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S);
     else if (S.mode == MD_MIXED) k_props_tiles<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S);
     else k_props_tiles<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S);
-    k_props_finalize<<<S.nrep, 256, 0, L.stream>>>(A, S, to_series ? 1 : 0, 0);
+    k_props_slices<<<S.nrep * PROPS_SPLIT, 256, 0, L.stream>>>(A, S);
+    k_props_finalize<<<S.nrep, 32, 0, L.stream>>>(A, S, to_series ? 1 : 0, 0);
     return cudaGetLastError();
 }
 

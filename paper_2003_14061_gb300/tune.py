@@ -1,0 +1,104 @@
+"""Autotuner for the launch shapes of an MDSystem.
+
+The paper found thread-block size to matter little on its GPU and warned that this need not hold
+elsewhere (Sec. 4.1 item 2).  On GB300 the residency of the fused step kernel and the number of
+neighbour-matrix loads each thread keeps in flight decide its speed, so they are measured on the
+system itself: every candidate advances the live system by a number of steps timed with CUDA
+events on the library's stream.  All candidates perform the same arithmetic in the same order,
+so tuning never changes the trajectory.
+
+Search: coordinate descent over (ctas_per_sm, nbr_batch) for the step kernel, then build_batch
+for the neighbour build (timed over steps that include rebuilds).  Results are cached per GPU
+and workload signature in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+CTAS = (4, 8, 12, 16)
+NBR_BATCH = (1, 2, 4)
+BUILD_BATCH = (1, 2, 4)
+
+
+def signature(system) -> str:
+    p = system.params
+    dev = torch.cuda.get_device_name(system.device)
+    return (f"{dev}|prec{p.precision}|n{system.n}|rep{system.nrep}|rc{p.rc:.4f}|skin{p.skin:.3f}|"
+            f"rho{system.n / float((system.boxes.prod(axis=1)).sum()):.3f}")
+
+
+def _time_steps(system, steps: int) -> float:
+    s = system.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    system.integrate(steps)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False) -> dict:
+    """Pick ctas_per_sm, nbr_batch and build_batch for this system; returns the choice and timings."""
+    key = signature(system)
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                best = table[key]["best"]
+                system.set_tuning(**best)
+                return table[key]
+        except (OSError, ValueError, KeyError):
+            pass
+    t_start = time.perf_counter()
+    steps = max(32, (steps // 16) * 16)           # whole 16-step graph replays
+    trials = {}
+
+    def trial(**kw):
+        system.set_tuning(**kw)
+        system.integrate(16)                       # capture the graph outside the timing
+        ms = _time_steps(system, steps)
+        trials[json.dumps(kw, sort_keys=True)] = ms
+        if verbose:
+            print(f"tune {kw}: {ms * 1e3:.1f} us/step", flush=True)
+        return ms
+
+    cur = system.tuning()
+    best = {"ctas_per_sm": cur["ctas_per_sm"], "nbr_batch": cur["nbr_batch"], "build_batch": cur["build_batch"]}
+    best_ms = trial(**best)
+    for ctas in CTAS:
+        for nb in NBR_BATCH:
+            cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb)
+            if json.dumps(cand, sort_keys=True) in trials:
+                continue
+            ms = trial(**cand)
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    for bb in BUILD_BATCH:
+        cand = dict(best, build_batch=bb)
+        if json.dumps(cand, sort_keys=True) in trials:
+            continue
+        ms = trial(**cand)
+        if ms < best_ms:
+            best, best_ms = cand, ms
+    system.set_tuning(**best)
+    result = {"best": best, "ms_per_step": best_ms, "trials": trials, "signature": key,
+              "seconds": time.perf_counter() - t_start}
+    if cache:
+        try:
+            table = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    table = json.load(f)
+            table[key] = result
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
+        except (OSError, ValueError):
+            pass
+    return result

@@ -7,6 +7,8 @@ Bars (from the workload definitions):
     <= 1e-4;
   * energy per particle: absolute difference <= 1e-6.
 """
+import json
+
 import numpy as np
 import pytest
 
@@ -149,6 +151,30 @@ def test_graph_and_direct_launches_agree_bitwise():
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     pa, pb = a.props()[0], b.props()[0]
     assert pa["rebuilds"] == pb["rebuilds"] and pa["step"] == pb["step"] == 100
+
+
+def test_launch_shapes_do_not_change_results():
+    ref, *_ = make("wca1372", "mixed")
+    ref.integrate(64)
+    xr, vr, _ = ref.state()
+    for ctas, nb, bb in ((4, 1, 1), (8, 4, 4), (16, 2, 2), (12, 1, 4)):
+        s, *_ = make("wca1372", "mixed")
+        s.set_tuning(ctas_per_sm=ctas, nbr_batch=nb, build_batch=bb)
+        s.integrate(64)
+        x, v, _ = s.state()
+        assert np.array_equal(x, xr) and np.array_equal(v, vr), (ctas, nb, bb)
+
+
+def test_autotuner_picks_a_measured_shape(tmp_path):
+    from paper_2003_14061_gb300 import tune
+    s, *_ = make("wca2048", "mixed")
+    res = tune.tune(s, steps=32, cache=str(tmp_path / "tune.json"))
+    assert res["best"] in [json.loads(k) for k in res["trials"]]
+    assert res["ms_per_step"] == min(res["trials"].values())
+    t = s.tuning()
+    assert all(t[k] == v for k, v in res["best"].items())
+    again = tune.tune(s, steps=32, cache=str(tmp_path / "tune.json"))      # served from the cache
+    assert again["best"] == res["best"]
 
 
 def test_energy_conservation_matches_oracle():
