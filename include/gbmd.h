@@ -191,6 +191,27 @@ typedef struct {
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);
 
+/* Reverse-mode derivative of a trajectory loss (the paper has no adjoint; this differentiates
+ * its method: the leapfrog of Sec. 4.3 item 1 and the pair force of Sec. 2.3).  Starting from
+ * the system's current state (x_0, v_0), S = nsteps kick-drift-kick steps are taken and
+ *     L = (1/S) sum_{n=1..S} U(x_n) + |v_S|^2
+ * is differentiated with respect to eps, sigma and every initial velocity.  The trajectory is run
+ * as segments of ckpt_every steps, each restarted from an FP64 checkpoint of (x, v); the reverse
+ * pass recomputes one segment at a time from its checkpoint (checkpoint-and-recompute) and walks
+ * it backwards with one force-Jacobian-vector-product kernel per step (FP32 pair arithmetic, FP64
+ * accumulation).  sigma moves the cutoff with it when r_c = 2^(1/6) sigma (WCA); otherwise r_c is
+ * held fixed.
+ *   d_work     : device scratch of md_adjoint_workspace_bytes(s, nsteps, ckpt_every) bytes,
+ *                256-byte aligned, owned by the caller (snapshots of one segment, checkpoints,
+ *                adjoint vectors).
+ *   loss, dL_deps, dL_dsigma : host doubles (each may be NULL).
+ *   dL_dv0     : [n][3] FP64 in id order, host or device (may be NULL).
+ * Needs nrep == 1 and MD_MIXED or MD_FP32.  Waits for the stream.  On return the system is back
+ * at (x_0, v_0) with its step and rebuild counters reset, as after md_set_state. */
+size_t md_adjoint_workspace_bytes(const md_system* s, int32_t nsteps, int32_t ckpt_every);
+int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, int32_t ckpt_every, double* loss,
+               double* dL_deps, double* dL_dsigma, double* dL_dv0);
+
 /* Per-phase timing (the breakdown of Table 2 of the paper: neighbour matrix, forces +
  * integration, layer/cell assignment, reorder, energy).  With timing enabled, every phase is
  * bracketed by CUDA events on the system's stream.  md_get_timing waits for the stream, then

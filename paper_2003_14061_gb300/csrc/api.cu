@@ -331,6 +331,18 @@ void fill_scal(md_system* s)
         uc = 4.0 * p.eps * (q6 * q6 - q6);
     }
     S.ucd = uc;
+    S.adj_eps144_over_sig = float(144.0 * p.eps / p.sigma);
+    S.adj_eps24_over_sig = float(24.0 * p.eps / p.sigma);
+    {
+        // du_c/dsigma: zero when r_c moves with sigma (the WCA cutoff 2^(1/6) sigma)
+        const bool scales = std::fabs(p.rc / p.sigma - std::pow(2.0, 1.0 / 6.0)) < 1e-9;
+        double duc = 0.0;
+        if (p.shift_energy && !scales) {
+            const double q2 = S.sig2d / S.rc2d, q6 = q2 * q2 * q2;
+            duc = 24.0 * p.eps * q6 * (2.0 * q6 - 1.0) / p.sigma;
+        }
+        S.adj_ducf = float(duc);
+    }
     S.rc2f = float(S.rc2d);
     S.rl2f = float(S.rl2d);
     S.sig2f = float(S.sig2d);
@@ -798,6 +810,194 @@ int md_get_tuning(const md_system* s, md_tuning* t)
     if (!s || !t) return fail(MD_ERR_INVALID_ARG, "bad arguments");
     *t = s->tune;
     return MD_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// adjoint driver
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct AdjPlan {
+    int K, S, nseg;
+};
+
+size_t carve_adj(const md_system* s, const AdjPlan& P, char* base, AdjView* V)
+{
+    Carver c{base};
+    AdjView v;
+    std::memset(&v, 0, sizeof(v));
+    const size_t ns = size_t(s->plan.nslots), n3 = size_t(s->plan.n_total) * 3;
+    v.pos_snap = c.take<float4>(ns * (P.K + 1));
+    v.cnt_snap = c.take<int32_t>(ns * (P.K + 1));
+    v.W_snap = c.take<uint32_t>(ns * size_t(s->plan.cap) * (P.K + 1));
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 3; ++a) {
+            v.lx[b][a] = c.take<double>(ns);
+            v.lv[b][a] = c.take<double>(ns);
+        }
+    v.tile_acc = c.take<double>(size_t(s->plan.ntiles) * 4);
+    v.ck_x = c.take<double>(n3 * (P.nseg + 1));
+    v.ck_v = c.take<double>(n3 * (P.nseg + 1));
+    v.lam_x = c.take<double>(n3);
+    v.lam_v = c.take<double>(n3);
+    v.vnorm_part = c.take<double>(ADJ_VPART);
+    v.out = c.take<double>(8);
+    if (V) *V = v;
+    return (c.off + 255) & ~size_t(255);
+}
+
+int adj_plan(const md_system* s, int32_t nsteps, int32_t ckpt_every, AdjPlan* P)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    if (s->plan.nrep != 1) return fail(MD_ERR_INVALID_ARG, "md_adjoint needs a single system (nrep == 1)");
+    if (s->plan.mode == MD_FP64) return fail(MD_ERR_INVALID_ARG, "md_adjoint runs on MD_MIXED or MD_FP32 systems");
+    if (nsteps < 1 || ckpt_every < 1 || ckpt_every > nsteps)
+        return fail(MD_ERR_INVALID_ARG, "need nsteps >= 1 and 1 <= ckpt_every <= nsteps");
+    P->K = ckpt_every;
+    P->S = nsteps;
+    P->nseg = (nsteps + ckpt_every - 1) / ckpt_every;
+    return MD_OK;
+}
+
+// positions and integer-step velocities (id order) into device buffers x, v
+int adj_save(md_system* s, const Scal& S, int cur, double* x, double* v)
+{
+    GBMD_CUDA(launch_forces(s->A, S, s->L, cur));
+    GBMD_CUDA(launch_get_state(s->A, S, s->L, cur, true, false));
+    const size_t bytes = size_t(s->plan.n_total) * 3 * sizeof(double);
+    GBMD_CUDA(cudaMemcpyAsync(x, s->A.xchg[0], bytes, cudaMemcpyDeviceToDevice, s->L.stream));
+    GBMD_CUDA(cudaMemcpyAsync(v, s->A.xchg[1], bytes, cudaMemcpyDeviceToDevice, s->L.stream));
+    return MD_OK;
+}
+
+// restart from a checkpoint: exact binning, reorder by cell, neighbour build
+int adj_load(md_system* s, const Scal& S, const double* x, const double* v)
+{
+    const size_t bytes = size_t(s->plan.n_total) * 3 * sizeof(double);
+    GBMD_CUDA(cudaMemcpyAsync(s->A.xchg[0], x, bytes, cudaMemcpyDeviceToDevice, s->L.stream));
+    GBMD_CUDA(cudaMemcpyAsync(s->A.xchg[1], v, bytes, cudaMemcpyDeviceToDevice, s->L.stream));
+    GBMD_CUDA(launch_set_state(s->A, S, s->L, 0));
+    GBMD_CUDA(launch_force_rebuild(s->A, S, s->L, 1));
+    GBMD_CUDA(launch_rebuild(s->A, S, s->L, 0, true));
+    return MD_OK;
+}
+
+int adj_step(md_system* s, const Scal& S, int& cur)
+{
+    Launch L = s->L;
+    L.use_cond = 0;
+    GBMD_CUDA(launch_step(s->A, S, L, cur, false));
+    cur ^= 1;
+    GBMD_CUDA(launch_bin_order(s->A, S, L, cur, false));
+    GBMD_CUDA(launch_reorder(s->A, S, L, cur));
+    GBMD_CUDA(launch_build_only(s->A, S, L, cur));
+    return MD_OK;
+}
+
+int adj_snapshot(md_system* s, const AdjView& V, int q, int cur)
+{
+    const size_t ns = size_t(s->plan.nslots);
+    GBMD_CUDA(cudaMemcpyAsync(V.pos_snap + ns * q, s->A.pos32[cur], ns * sizeof(float4), cudaMemcpyDeviceToDevice,
+                              s->L.stream));
+    GBMD_CUDA(cudaMemcpyAsync(V.cnt_snap + ns * q, s->A.nbr_count, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                              s->L.stream));
+    GBMD_CUDA(cudaMemcpyAsync(V.W_snap + ns * size_t(s->plan.cap) * q, s->A.W, ns * size_t(s->plan.cap) * sizeof(uint32_t),
+                              cudaMemcpyDeviceToDevice, s->L.stream));
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t md_adjoint_workspace_bytes(const md_system* s, int32_t nsteps, int32_t ckpt_every)
+{
+    AdjPlan P;
+    if (adj_plan(s, nsteps, ckpt_every, &P) != MD_OK) return 0;
+    return carve_adj(s, P, nullptr, nullptr);
+}
+
+int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, int32_t ckpt_every, double* loss,
+               double* dL_deps, double* dL_dsigma, double* dL_dv0)
+{
+    AdjPlan P;
+    int rc = adj_plan(s, nsteps, ckpt_every, &P);
+    if (rc) return rc;
+    const size_t need = carve_adj(s, P, nullptr, nullptr);
+    if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u) || work_bytes < need)
+        return fail(MD_ERR_WORKSPACE, "adjoint workspace missing, misaligned or below " + std::to_string(need) + " bytes");
+    AdjView V;
+    carve_adj(s, P, static_cast<char*>(d_work), &V);
+    if (s->binned_fresh) {
+        GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
+        s->binned_fresh = false;
+    }
+    // inside a segment the slot order must stay fixed: no reorder (the restart reorders)
+    Scal Sa = s->S;
+    Sa.reorder_every = 0x7fffffff;
+    const size_t n3 = size_t(s->plan.n_total) * 3;
+    cudaStream_t st = s->L.stream;
+    Phase tph(s, MD_PHASE_OTHER, 0);
+
+    // forward: checkpoints of (x, v) at the start of every segment and at the end
+    rc = adj_save(s, s->S, s->cur, V.ck_x, V.ck_v);
+    if (rc) return rc;
+    for (int k = 0; k < P.nseg; ++k) {
+        rc = adj_load(s, Sa, V.ck_x + n3 * k, V.ck_v + n3 * k);
+        if (rc) return rc;
+        int cur = 0;
+        const int steps = std::min(P.K, P.S - k * P.K);
+        for (int q = 1; q <= steps; ++q) {
+            rc = adj_step(s, Sa, cur);
+            if (rc) return rc;
+        }
+        rc = adj_save(s, Sa, cur, V.ck_x + n3 * (k + 1), V.ck_v + n3 * (k + 1));
+        if (rc) return rc;
+    }
+    // terminal conditions and the |v_S|^2 part of the loss
+    GBMD_CUDA(launch_adj_init(V, s->L, s->plan.n_total, V.ck_v + n3 * P.nseg));
+    GBMD_CUDA(cudaMemsetAsync(V.tile_acc, 0, sizeof(double) * 4 * size_t(s->plan.ntiles), st));
+    // reverse, one segment at a time: recompute it from its checkpoint, then walk back
+    int buf = 0;
+    for (int k = P.nseg - 1; k >= 0; --k) {
+        rc = adj_load(s, Sa, V.ck_x + n3 * k, V.ck_v + n3 * k);
+        if (rc) return rc;
+        int cur = 0;
+        rc = adj_snapshot(s, V, 0, cur);
+        if (rc) return rc;
+        const int steps = std::min(P.K, P.S - k * P.K);
+        for (int q = 1; q <= steps; ++q) {
+            rc = adj_step(s, Sa, cur);
+            if (!rc) rc = adj_snapshot(s, V, q, cur);
+            if (rc) return rc;
+        }
+        GBMD_CUDA(launch_adj_permute(s->A, Sa, s->L, V, buf, true));
+        for (int q = steps; q >= 1; --q) {
+            const int n = k * P.K + q;
+            const double kappa = (n == P.S) ? 1.0 : 2.0;
+            GBMD_CUDA(launch_adj_reverse(s->A, Sa, s->L, V, q, kappa, 1.0 / double(P.S), buf));
+            buf ^= 1;
+        }
+        if (k == 0) {
+            GBMD_CUDA(launch_adj_reverse(s->A, Sa, s->L, V, 0, 1.0, 0.0, buf));
+            buf ^= 1;
+        }
+        GBMD_CUDA(launch_adj_permute(s->A, Sa, s->L, V, buf, false));
+    }
+    GBMD_CUDA(launch_adj_final(V, s->L, s->plan.ntiles));
+    double out[8];
+    GBMD_CUDA(cudaMemcpyAsync(out, V.out, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+    if (dL_dv0) GBMD_CUDA(cudaMemcpyAsync(dL_dv0, V.lam_v, sizeof(double) * n3, cudaMemcpyDefault, st));
+    // leave the system at its initial state
+    rc = load_state(s, V.ck_x, V.ck_v);
+    if (rc) return rc;
+    GBMD_CUDA(cudaStreamSynchronize(st));
+    if (loss) *loss = out[2] + out[4];
+    if (dL_deps) *dL_deps = (out[0] + out[2]) / s->p.eps;
+    if (dL_dsigma) *dL_dsigma = out[1] + out[3];
+    return latch_error(s);
 }
 
 }  // extern "C"

@@ -32,6 +32,7 @@ constexpr int64_t MAX_SLOTS = int64_t(1) << 26;
 constexpr int MAX_NC = 1023;
 constexpr int SCAN_CHUNK = 2048;          // cells per block of the prefix sum
 constexpr int PROPS_SPLIT = 32;           // CTAs per replica in the first level of the final sums
+constexpr int ADJ_VPART = 128;            // blocks of the |v_S|^2 partial sums
 
 enum ErrBits { ERR_NBR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
@@ -132,6 +133,23 @@ struct Scal {
     double disp_margin;       // rounding margin of a displacement measured on FP32 positions
     double rc2d, rl2d, sig2d, eps4d, eps48d, ucd;
     float rc2f, rl2f, sig2f, eps4f, eps48f, ucf;
+    float adj_eps144_over_sig, adj_eps24_over_sig, adj_ducf;   // sigma-derivative constants
+};
+
+// adjoint workspace (md_adjoint), carved from the caller's second buffer
+struct AdjView {
+    float4* pos_snap;         // [K+1][nslots] positions of the segment's steps
+    int32_t* cnt_snap;        // [K+1][nslots] neighbour counts
+    uint32_t* W_snap;         // [K+1][cap][nslots] neighbour matrices
+    double* lx[2][3];         // adjoint of positions, slot order, ping-pong
+    double* lv[2][3];         // adjoint of velocities
+    double* tile_acc;         // [ntiles][4] running sums of the parameter terms and the loss
+    double* ck_x;             // [nseg+1][n][3] FP64 checkpoints, id order
+    double* ck_v;
+    double* lam_x;            // [n][3] adjoint state in id order between segments
+    double* lam_v;
+    double* vnorm_part;       // [ADJ_VPART]
+    double* out;              // [8]
 };
 
 // ------------------------------------------------------------------------------------------
@@ -209,6 +227,13 @@ cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int
 cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);   // 6 kernels
 cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur);                    // 2 kernels
 cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur);                // 2 kernels
+
+// adjoint (kernels_adjoint.cu)
+cudaError_t launch_adj_reverse(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int q, double kappa,
+                               double w_U, int in_buf);
+cudaError_t launch_adj_permute(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int buf, bool to_slot);
+cudaError_t launch_adj_init(const AdjView& V, const Launch& L, int64_t n, const double* vS);
+cudaError_t launch_adj_final(const AdjView& V, const Launch& L, int ntiles);
 
 // step path (kernels_step.cu)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props);

@@ -180,6 +180,27 @@ class MDSystem:
     def check(self):
         self._call("md_check")
 
+    def adjoint(self, nsteps: int, ckpt_every: int = 20, dv0_out: torch.Tensor = None):
+        """Loss L = (1/S) sum_{n=1..S} U(x_n) + |v_S|^2 and (dL/deps, dL/dsigma, dL/dv0).
+
+        The state is left at its initial value.  dv0_out (float64 [n,3], device or pinned host)
+        receives dL/dv0 in place; otherwise a numpy array is returned."""
+        nb = self.lib.md_adjoint_workspace_bytes(self.h, int(nsteps), int(ckpt_every))
+        if nb == 0:
+            raise B.MDError(-1, "md_adjoint_workspace_bytes", B.last_error())
+        if getattr(self, "_adj_ws", None) is None or self._adj_ws.numel() < nb:
+            with torch.cuda.device(self.device):
+                self._adj_ws = torch.empty(int(nb), dtype=torch.uint8, device=self.device)
+        loss, ge, gs = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        if dv0_out is not None:
+            gv, gptr = dv0_out, ctypes.c_void_p(dv0_out.data_ptr())
+        else:
+            gv = np.zeros((self.n, 3))
+            gptr = gv.ctypes.data_as(ctypes.c_void_p)
+        self._call("md_adjoint", ctypes.c_void_p(self._adj_ws.data_ptr()), int(self._adj_ws.numel()), int(nsteps),
+                   int(ckpt_every), ctypes.byref(loss), ctypes.byref(ge), ctypes.byref(gs), gptr)
+        return loss.value, ge.value, gs.value, gv
+
     def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0):
         """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct."""
         t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph))
