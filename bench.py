@@ -296,7 +296,105 @@ def run_gb300(args, rank, world, local_rank):
             "kernel_ms_per_launch": per_launch_ms,
         }
     s.close()
+    if rank == 0 and world == 1 and args.forms and not args.ncell:
+        result["forms"] = measure_forms(args, dev)
     return result
+
+
+def _event_ms(s, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    fn()
+    e1.record(s.stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune=True):
+    """Particle-steps/s of one form of the hot path, with its step-kernel roofline fraction."""
+    from paper_2003_14061_gb300 import tune as gtune
+    from paper_2003_14061_gb300.system import MDSystem
+    s = MDSystem(x, v, device=dev, rc=rc, skin=skin, dt=DT, precision=precision, reorder_every=100, **geo)
+    s.integrate(max(warmup // 2, 16))
+    if tune:
+        gtune.tune(s, steps=64)
+    s.integrate(max(warmup // 2, 16))
+    p0 = s.props()
+    ms = _event_ms(s, lambda: s.integrate(steps))
+    p1 = s.props()
+    n = s.n
+    mean_nbrs = float(np.average([p["mean_nbrs"] for p in p1], weights=s.n_rep))
+    s.set_tuning(use_graph=2)
+    s.set_timing(True)
+    s.integrate(min(steps, 200))
+    ph = s.timing()
+    s.set_timing(False)
+    step_ms = ph["step"][0] / max(ph["step"][1], 1)
+    peak, kind = load_peaks()
+    bpa = algorithmic_bytes_per_atom_step(mean_nbrs, precision)
+    achieved = bpa * n / (step_ms * 1e-3) / 1e9
+    out = {"label": label, "value": n * steps / (ms * 1e-3), "unit": UNIT, "atoms": n, "replicas": s.nrep,
+           "steps": steps, "ms_per_step": ms / steps, "precision": precision, "mean_neighbours": mean_nbrs,
+           "rebuilds_per_100_steps": 100.0 * sum(a["rebuilds"] - b["rebuilds"] for a, b in zip(p1, p0)) / s.nrep / steps,
+           "kernel_ms_per_launch": step_ms, "tuning": s.tuning(),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "bytes_per_atom": bpa, "peak_kind": kind},
+           "energy_per_atom": float(np.average([p["E_per_atom"] for p in p1], weights=s.n_rep))}
+    s.close()
+    return out
+
+
+def measure_forms(args, dev):
+    """The other forms of the hot path, each reported beside the main line."""
+    from paper_2003_14061_gb300 import inputs
+    from paper_2003_14061_gb300.system import MDSystem
+    forms = {}
+    t0 = time.perf_counter()
+    # plain FP32 (pair forces and state) on the main workload
+    x, v, geo = make_inputs("wca4m")
+    forms["wca4m_fp32"] = measure_form("WCA fcc 100^3, FP32 state", x, v, geo, dev, "fp32", WCA_RC, 0.4,
+                                       args.form_steps, 200)
+    # the LJ liquid (r_c = 2.5, shifted), 16,384,000 atoms
+    w = WORKLOADS["lj16m"]
+    x, v, geo = make_inputs("lj16m")
+    forms["lj16m_mixed"] = measure_form(w["desc"], x, v, geo, dev, "mixed", w["rc"], w["skin"],
+                                        max(args.form_steps // 4, 100), 100)
+    del x, v
+    # 512 independent replicas of uneven size in one persistent launch per step
+    w = WORKLOADS["batch512"]
+    x, v, geo = make_inputs("batch512")
+    forms["batch512_mixed"] = measure_form(w["desc"], x, v, geo, dev, "mixed", w["rc"], w["skin"],
+                                           args.form_steps, 200)
+    # FP64 cell list (skin 0, rebuilt every step), 2048 atoms: L2-resident, steps/s is the figure
+    xl, box = inputs.fcc_lattice(8, 0.8)
+    vl = inputs.maxwell(xl.shape[0], 1.0, 1)
+    s = MDSystem(xl, vl, box, device=dev, rc=WCA_RC, skin=0.0, dt=DT, precision="fp64", reorder_every=100)
+    s.integrate(100)
+    ms = _event_ms(s, lambda: s.integrate(1000))
+    forms["wca2048_fp64_celllist"] = {"label": "WCA fcc 8^3 = 2048 atoms, FP64, cell list rebuilt every step",
+                                      "value": 2048 * 1000 / (ms * 1e-3), "unit": UNIT,
+                                      "steps_per_s": 1000 / (ms * 1e-3), "ms_per_step": ms / 1000,
+                                      "note": "working set in L2; no HBM roofline"}
+    s.close()
+    # adjoint: 32,000 atoms, 400 steps, checkpoints every 20
+    xa, boxa = inputs.fcc_subset(32000, 0.8, seed=5)
+    va = inputs.maxwell(32000, 1.0, seed=6)
+    s = MDSystem(xa, va, boxa, device=dev, rc=WCA_RC, skin=0.4, dt=DT, precision="mixed")
+    s.adjoint(400, 20)                                     # warm-up (workspace, lazy loads)
+    import torch
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s.adjoint(400, 20)
+    secs = time.perf_counter() - t
+    forms["adjoint32k"] = {"label": "adjoint, WCA 32,000 atoms, 400 steps, checkpoints every 20",
+                           "value": 400 / secs, "unit": "grad-steps/s", "seconds_per_gradient": secs,
+                           "particle_grad_steps_per_s": 32000 * 400 / secs,
+                           "note": "a grad-step = forward step + recomputed step + reverse step; working set in L2"}
+    s.close()
+    forms["seconds"] = time.perf_counter() - t0
+    return forms
 
 
 def run_reference(args):
@@ -350,6 +448,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--tune", type=int, default=1, help="1: autotune launch shapes during warm-up")
     ap.add_argument("--tune-steps", type=int, default=128)
+    ap.add_argument("--forms", type=int, default=1, help="1: also measure the FP32, LJ, batched, FP64 and adjoint forms")
+    ap.add_argument("--form-steps", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--phase-steps", type=int, default=400)
     ap.add_argument("--cpu-steps", type=int, default=10)
