@@ -198,12 +198,12 @@ def run_gb300(args, rank, world, local_rank):
     props = s.props()
     rebuilds_timed = sum(p["rebuilds"] - r0 for p, r0 in zip(props, rb0))
     # kernels that ran: the host-issued ones plus, inside captured graphs, the 10 kernels of
-    # every rebuild whose IF node opened (a batch runs one rebuild sequence for all replicas)
+    # every rebuild whose IF node opened (11 kernels; a batch runs one sequence for all replicas)
     graph_mode = s.tuning()["use_graph"] == 1
     launches = sum(p[2] for p in issued.values())
     if graph_mode:
         nrb = max(p["rebuilds"] - r0 for p, r0 in zip(props, rb0)) if s.nrep == 1 else rebuilds_timed
-        launches += 10 * int(nrb)
+        launches += 11 * int(nrb)
     mean_nbrs = float(np.average([p["mean_nbrs"] for p in props], weights=s.n_rep))
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)

@@ -185,7 +185,9 @@ typedef struct {
                                 the step kernel is also compiled to fit 4, 8, 12 or 16 CTAs per SM
                                 (the largest not above this) and its grid is capped at residency */
     int32_t nbr_batch;       /* W entries each thread loads together in the pair loop: 1, 2 or 4 */
-    int32_t build_batch;     /* candidate atoms each thread loads together in the build: 1, 2 or 4 */
+    int32_t build_batch;     /* neighbour build: 1, 2 or 4 = one thread per atom loading that many
+                                candidates together; 32 = one warp per cell, candidates shared
+                                by warp shuffles (for cells of tens of atoms) */
     int32_t use_graph;       /* 1: md_integrate replays captured CUDA graphs; 2: direct launches */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);

@@ -32,6 +32,7 @@ struct Plan {
     int32_t nrep = 0;
     std::vector<Rep> reps;
     std::vector<int32_t> tile_rep;
+    std::vector<int32_t> cell_rep;
     int64_t nslots = 0;
     int32_t ntiles = 0;
     int32_t ncells = 0;
@@ -125,6 +126,9 @@ int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const doub
     P->tile_rep.resize(P->ntiles);
     for (int32_t r = 0; r < nrep; ++r)
         for (int32_t k = 0; k < P->reps[r].ntiles; ++k) P->tile_rep[P->reps[r].tile0 + k] = r;
+    P->cell_rep.resize(size_t(P->ncells));
+    for (int32_t r = 0; r < nrep; ++r)
+        for (int32_t k = 0; k < P->reps[r].ncells; ++k) P->cell_rep[size_t(P->reps[r].cell0) + k] = r;
     if (p->nbr_capacity > 0) {
         P->cap = p->nbr_capacity;
     } else {
@@ -171,6 +175,9 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.cstart = c.take<int32_t>(size_t(P.ncells) + 1);
     a.chunk = c.take<int32_t>(size_t(P.nchunks));
     a.tile_rep = c.take<int32_t>(size_t(P.ntiles));
+    a.rb_tiles = c.take<int32_t>(size_t(P.ntiles));
+    a.cell_rep = c.take<int32_t>(size_t(P.ncells));
+    a.rb_base = c.take<int32_t>(size_t(P.nrep));
     a.tile_part = c.take<double>(size_t(P.ntiles) * NPROP);
     a.slice_part = c.take<double>(size_t(P.nrep) * PROPS_SPLIT * NPROP);
     a.rep = c.take<Rep>(size_t(P.nrep));
@@ -213,6 +220,7 @@ struct md_system {
     size_t ws_bytes = 0;
     // per-phase timers (CUDA events on the system's stream) and kernel-launch counts
     bool timing = false;
+    long long graph_rebuilds_seen = 0;
     std::vector<EvPair> pending;
     std::vector<cudaEvent_t> pool;
     double ms[MD_NPHASE] = {0};
@@ -442,6 +450,7 @@ int capture_graph(md_system* s, int cur0)
             Launch Lb = s->L;
             Lb.stream = s->aux;
             Lb.use_cond = 0;
+            Lb.in_graph = 1;
             cudaError_t e2 = launch_bin_order(s->A, s->S, Lb, cur, false);
             if (e2 == cudaSuccess) e2 = launch_reorder(s->A, s->S, Lb, cur);
             if (e2 == cudaSuccess) e2 = launch_build_only(s->A, s->S, Lb, cur);
@@ -537,6 +546,8 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     if (cudaMemcpyAsync(s->A.rep, s->plan.reps.data(), sizeof(Rep) * s->plan.nrep, cudaMemcpyHostToDevice,
                         s->L.stream) != cudaSuccess ||
         cudaMemcpyAsync(s->A.tile_rep, s->plan.tile_rep.data(), sizeof(int32_t) * s->plan.ntiles,
+                        cudaMemcpyHostToDevice, s->L.stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->A.cell_rep, s->plan.cell_rep.data(), sizeof(int32_t) * s->plan.ncells,
                         cudaMemcpyHostToDevice, s->L.stream) != cudaSuccess)
         return bail(fail(MD_ERR_CUDA, "upload of the replica table"));
     rc = load_state(s, x0, v0);
@@ -628,7 +639,7 @@ int md_integrate(md_system* s, int32_t nsteps)
         }
         s->cur ^= 1;
         {
-            Phase t(s, MD_PHASE_BIN, 6);
+            Phase t(s, MD_PHASE_BIN, 7);
             GBMD_CUDA(launch_bin_order(s->A, s->S, s->L, s->cur, false));
         }
         {
@@ -655,6 +666,13 @@ int md_get_timing(md_system* s, double* ms, int64_t* calls, int64_t* launches)
 {
     if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
     GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    {
+        // rebuild sequences inside graphs ran only when their IF node opened: count them here
+        long long gr = 0;
+        GBMD_CUDA(cudaMemcpy(&gr, &s->A.g->graph_rebuilds, sizeof(gr), cudaMemcpyDeviceToHost));
+        s->launches[MD_PHASE_BUILD] += REBUILD_KERNELS * (gr - s->graph_rebuilds_seen);
+        s->graph_rebuilds_seen = gr;
+    }
     for (auto& pr : s->pending) {
         float t = 0.0f;
         GBMD_CUDA(cudaEventElapsedTime(&t, pr.a, pr.b));
@@ -794,8 +812,8 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(MD_ERR_INVALID_ARG, "ctas_per_sm in 0..64");
     if (t->nbr_batch && t->nbr_batch != 1 && t->nbr_batch != 2 && t->nbr_batch != 4)
         return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 1, 2 or 4");
-    if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4)
-        return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2 or 4");
+    if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
+        return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2, 4 or 32");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;

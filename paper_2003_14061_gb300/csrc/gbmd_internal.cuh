@@ -74,6 +74,9 @@ struct Global {               // device-wide words
     int32_t any_reorder;      // some rebuilding replica reorders
     int32_t err;              // ErrBits, latched
     int32_t max_nbr_seen;     // largest m_i that overflowed
+    int32_t n_rb_tiles;       // entries of rb_tiles for the rebuild in progress
+    int32_t pad;
+    long long graph_rebuilds; // rebuild sequences that ran inside captured graphs
 };
 
 struct Arrays {
@@ -104,6 +107,9 @@ struct Arrays {
     int32_t* chunk;           // per SCAN_CHUNK cells
     // per tile
     int32_t* tile_rep;
+    int32_t* rb_tiles;        // tiles of the replicas rebuilding in this step
+    int32_t* cell_rep;        // replica of every (global) cell
+    int32_t* rb_base;         // per replica: its first entry in rb_tiles
     double* tile_part;        // NPROP per tile
     double* slice_part;       // NPROP per (replica, slice) of the final sums
     // per replica
@@ -215,6 +221,7 @@ struct Launch {
     int build_batch;          // candidates loaded together per thread in the build (1, 2, 4)
     cudaGraphConditionalHandle cond;   // IF node of the rebuild (inside a captured graph)
     int use_cond;             // 1 while capturing md_integrate into a graph
+    int in_graph;             // 1 while capturing an IF-node body (counts rebuild sequences)
 };
 
 // records msg for md_last_error() on this thread and returns code (api.cu)
@@ -224,9 +231,10 @@ int set_last_error(int code, const char* msg);
 cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder);
 cudaError_t launch_rebuild(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
 cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
-cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);   // 6 kernels
+cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);   // 7 kernels
 cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur);                    // 2 kernels
 cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur);                // 2 kernels
+constexpr int REBUILD_KERNELS = 11;       // kernels of one rebuild sequence (bin/order 7, reorder 2, build 2)
 
 // adjoint (kernels_adjoint.cu)
 cudaError_t launch_adj_reverse(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int q, double kappa,

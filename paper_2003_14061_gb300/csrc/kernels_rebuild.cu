@@ -48,23 +48,70 @@ __device__ void flush_stats(int64_t* sum_dst, int* max_dst, long long sum, int m
 }
 
 // ------------------------------------------------------------------------------------------
+// The tiles of the replicas that rebuild in this step, listed contiguously so that the rebuild
+// kernels share them evenly among their CTAs (in a batch only some replicas rebuild per step).
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_rebuild_list(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    __shared__ int sh[33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int carry = 0;
+    for (int r0 = 0; r0 < S.nrep; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        const int v = (r < S.nrep && A.rs[r].rebuild) ? A.rep[r].ntiles : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) sh[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int wv = sh[lane];
+            int wi = wv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            sh[lane] = wi - wv;
+            if (lane == 31) sh[32] = wi;
+        }
+        __syncthreads();
+        if (r < S.nrep) A.rb_base[r] = carry + sh[wid] + incl - v;
+        carry += sh[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A.g->n_rb_tiles = carry;
+    // fill: replica by replica, all threads writing its consecutive tiles
+    for (int r = 0; r < S.nrep; ++r) {
+        if (!A.rs[r].rebuild) continue;
+        const int base = A.rb_base[r], t0 = A.rep[r].tile0, nt = A.rep[r].ntiles;
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) A.rb_tiles[base + k] = t0 + k;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // N1 + N2
 // ------------------------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int from_set)
 {
     if (!A.g->any_rebuild) return;
-    const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(S.ntiles, t_begin + per);
+    const int nrb = A.g->n_rb_tiles;                  // tiles of the rebuilding replicas
+    const int per = (nrb + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(nrb, t_begin + per);
     int run_r = -1, run_occ = 0;
-    for (int t = t_begin; t < t_end; ++t) {
+    for (int it = t_begin; it < t_end; ++it) {
+        const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
         if (r != run_r) {
             if (run_r >= 0) flush_stats(nullptr, &A.rs[run_r].max_occ, 0, run_occ);
             run_r = r;
             run_occ = 0;
         }
-        if (!A.rs[r].rebuild) continue;
         const Rep& R = A.rep[r];
         if (t == R.tile0 && threadIdx.x == 0) {
             A.rs[r].sum_nbrs = 0;
@@ -283,9 +330,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(Arrays A, Scal S)
 __global__ void __launch_bounds__(TILE) k_scatter(Arrays A, Scal S)
 {
     if (!A.g->any_rebuild) return;
-    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    const int nrb = A.g->n_rb_tiles;
+    for (int it = blockIdx.x; it < nrb; it += gridDim.x) {
+        const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
-        if (!A.rs[r].rebuild) continue;
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         if (slot - R.slot0 < R.n) A.perm[A.cstart[A.cell[slot]] + A.layer[slot]] = int32_t(slot);
@@ -317,9 +365,11 @@ template <int MODE>
 __global__ void __launch_bounds__(TILE) k_reorder_gather(Arrays A, Scal S, int cur)
 {
     if (!A.g->any_reorder) return;
-    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    const int nrb = A.g->n_rb_tiles;
+    for (int it = blockIdx.x; it < nrb; it += gridDim.x) {
+        const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
-        if (!(A.rs[r].rebuild && A.rs[r].reorder)) continue;
+        if (!A.rs[r].reorder) continue;
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         const int64_t j = slot - R.slot0;
@@ -345,9 +395,11 @@ template <int MODE>
 __global__ void __launch_bounds__(TILE) k_reorder_copy(Arrays A, Scal S, int cur)
 {
     if (!A.g->any_reorder) return;
-    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+    const int nrb = A.g->n_rb_tiles;
+    for (int it = blockIdx.x; it < nrb; it += gridDim.x) {
+        const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
-        if (!(A.rs[r].rebuild && A.rs[r].reorder)) continue;
+        if (!A.rs[r].reorder) continue;
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         const int64_t j = slot - R.slot0;
@@ -399,11 +451,13 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
     if constexpr (sizeof(T) == 8) pos = reinterpret_cast<const P4*>(A.pos64[cur]);
     else pos = reinterpret_cast<const P4*>(A.pos32[cur]);
     const T rl2 = (sizeof(T) == 8) ? T(S.rl2d) : T(S.rl2f);
-    const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(S.ntiles, t_begin + per);
+    const int nrb = A.g->n_rb_tiles;                  // tiles of the rebuilding replicas
+    const int per = (nrb + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(nrb, t_begin + per);
     int run_r = -1, run_max = 0;
     long long run_sum = 0;
-    for (int t = t_begin; t < t_end; ++t) {
+    for (int it = t_begin; it < t_end; ++it) {
+        const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
         if (r != run_r) {
             if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
@@ -411,7 +465,6 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
             run_sum = 0;
             run_max = 0;
         }
-        if (!A.rs[r].rebuild) continue;
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         const bool active = slot - R.slot0 < R.n;
@@ -426,21 +479,38 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
             const int xm = (cx == 0) ? R.nc[0] - 1 : cx - 1;
             const int xp = (cx == R.nc[0] - 1) ? 0 : cx + 1;
             uint32_t* wp = A.W + slot;         // next free entry of this atom's column of W
+            // Squared distance from the atom to the lower and upper faces of its cell, per axis:
+            // a neighbouring cell whose nearest point is farther than r_c + skin cannot hold a
+            // neighbour.  The relative margin keeps this strictly looser than the criterion below.
+            const T lc[3] = {pi.x, pi.y, pi.z};
+            T dlo2[3], dhi2[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                dlo2[a] = lc[a] * lc[a];
+                dhi2[a] = (w[a] - lc[a]) * (w[a] - lc[a]);
+            }
+            const T skip2 = rl2 * ((sizeof(T) == 8) ? T(1.0 + 1e-12) : T(1.0f + 1e-5f));
             for (int oz = -1; oz <= 1; ++oz) {
                 int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
                 const T offz = T(oz) * w[2];
                 for (int oy = -1; oy <= 1; ++oy) {
                     int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
                     const T offy = T(oy) * w[1];
+                    const T dyz = ((oy < 0) ? dlo2[1] : ((oy > 0) ? dhi2[1] : T(0))) +
+                                  ((oz < 0) ? dlo2[2] : ((oz > 0) ? dhi2[2] : T(0)));
+                    if (dyz > skip2) continue;
+                    const bool use_l = dyz + dlo2[0] <= skip2, use_r = dyz + dhi2[0] <= skip2;
                     const int row = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0];
                     const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
                     // the three cells of this row, as [b0,e0) [b1,e1) [b2,e2) in perm; without a
                     // periodic wrap in x they are one contiguous range [b0, e2) split at b1, b2
-                    const int b0 = A.cstart[row + xm], e0 = A.cstart[row + xm + 1];
+                    const int b0 = A.cstart[row + xm], e0 = use_l ? A.cstart[row + xm + 1] : b0;
                     const int b1 = A.cstart[row + cx], e1 = A.cstart[row + cx + 1];
-                    const int b2 = A.cstart[row + xp], e2 = A.cstart[row + xp + 1];
+                    const int b2 = A.cstart[row + xp], e2 = use_r ? A.cstart[row + xp + 1] : b2;
                     if (cx > 0 && cx < R.nc[0] - 1) {
-                        for (int k0 = b0; k0 < e2; k0 += BB) {
+                        // consecutive cells: one range, starting past the left cell if it is skipped
+                        const int kb = use_l ? b0 : b1;
+                        for (int k0 = kb; k0 < e2; k0 += BB) {
                             int32_t js[BB];
 #pragma unroll
                             for (int u = 0; u < BB; ++u) js[u] = A.perm[min(k0 + u, e2 - 1)];
@@ -517,10 +587,204 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
     if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
 }
 
+
+// ------------------------------------------------------------------------------------------
+// N5 for dense cells (tens of atoms per cell, e.g. the LJ liquid at r_c + skin = 2.8): one warp
+// per cell, one lane per atom of it.  The candidates of each 3-cell row of the 27-cell
+// neighbourhood are staged once in the warp's shared memory (coalesced loads, double-buffered:
+// the next row is loaded while the current one is tested), and every lane tests them with
+// broadcast reads, so no candidate is fetched per lane and no lane diverges.  The displacement
+// is the criterion's expression (p_j - p_i) + o w, o constant per cell.  Rows and cells no lane
+// of the warp can reach are skipped by a warp vote.
+// ------------------------------------------------------------------------------------------
+constexpr int CW_WARPS = TILE / 32;
+constexpr int CW_ROW = 128;                    // candidates of one row staged at a time
+constexpr int CW_PER_LANE = CW_ROW / 32;
+
+struct CwRow {
+    int b[3], n[3];                           // the three cells of the row as perm ranges
+    int tot;
+};
+
+__device__ __forceinline__ int cw_index(const CwRow& R, int q)
+{
+    return (q < R.n[0]) ? R.b[0] + q : ((q < R.n[0] + R.n[1]) ? R.b[1] + (q - R.n[0]) : R.b[2] + (q - R.n[0] - R.n[1]));
+}
+
+__global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_rebuild) return;
+    __shared__ float4 s_p[CW_WARPS][2][CW_ROW];
+    __shared__ int32_t s_j[CW_WARPS][2][CW_ROW];
+    const float4* __restrict__ pos = A.pos32[cur];
+    const float rl2 = S.rl2f;
+    const float skip2 = rl2 * (1.0f + 1e-5f);
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int per = (S.ncells + nw - 1) / nw;
+    const int c_begin = gw * per, c_end = min(S.ncells, c_begin + per);
+    int run_r = -1, run_max = 0;
+    long long run_sum = 0;
+    for (int c = c_begin; c < c_end; ++c) {
+        const int r = A.cell_rep[c];
+        if (r != run_r) {
+            if (run_r >= 0) {
+                const long long ws = warp_sum_ll(run_sum);
+                const int wm = warp_max_i(run_max);
+                if (lane == 0) {
+                    if (ws) atomicAdd(reinterpret_cast<unsigned long long*>(&A.rs[run_r].sum_nbrs),
+                                      static_cast<unsigned long long>(ws));
+                    if (wm > 0) atomicMax(&A.rs[run_r].max_nbrs, wm);
+                }
+            }
+            run_r = r;
+            run_sum = 0;
+            run_max = 0;
+        }
+        if (!A.rs[r].rebuild) continue;
+        const Rep& R = A.rep[r];
+        const int cl = c - R.cell0;
+        const int cx = cl % R.nc[0], cy = (cl / R.nc[0]) % R.nc[1], cz = cl / (R.nc[0] * R.nc[1]);
+        const int xs[3] = {(cx == 0) ? R.nc[0] - 1 : cx - 1, cx, (cx == R.nc[0] - 1) ? 0 : cx + 1};
+        const float w0 = R.wf[0], w1 = R.wf[1], w2 = R.wf[2];
+        const int ab = A.cstart[c], ae = A.cstart[c + 1];
+        for (int a0 = ab; a0 < ae; a0 += 32) {
+            const bool have = a0 + lane < ae;
+            const int i = have ? A.perm[a0 + lane] : -1;
+            const float4 pi = have ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float dl[3] = {pi.x * pi.x, pi.y * pi.y, pi.z * pi.z};
+            const float dh[3] = {(w0 - pi.x) * (w0 - pi.x), (w1 - pi.y) * (w1 - pi.y), (w2 - pi.z) * (w2 - pi.z)};
+            int m = 0;
+            uint32_t* wp = A.W + (have ? i : 0);
+            // the 9 rows (oy, oz) and their cells, with the ones no lane can reach removed
+            auto row_of = [&](int rr, CwRow& Q) {
+                const int oy = rr % 3 - 1, oz = rr / 3 - 1;
+                int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
+                int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
+                const float dyz = ((oy < 0) ? dl[1] : ((oy > 0) ? dh[1] : 0.f)) + ((oz < 0) ? dl[2] : ((oz > 0) ? dh[2] : 0.f));
+                const int rowc = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0];
+                Q.tot = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float dd = dyz + ((k == 0) ? dl[0] : ((k == 2) ? dh[0] : 0.f));
+                    const bool need = __any_sync(0xffffffffu, have && dd <= skip2);
+                    const int gc = rowc + xs[k];
+                    Q.b[k] = A.cstart[gc];
+                    Q.n[k] = need ? A.cstart[gc + 1] - Q.b[k] : 0;
+                    Q.tot += Q.n[k];
+                }
+            };
+            CwRow cur_row, nxt_row;
+            int32_t rj[CW_PER_LANE];
+            float4 rp[CW_PER_LANE];
+            auto load_regs = [&](const CwRow& Q, int q0) {
+#pragma unroll
+                for (int u = 0; u < CW_PER_LANE; ++u) {
+                    const int q = q0 + lane + 32 * u;
+                    rj[u] = (q < Q.tot) ? A.perm[cw_index(Q, q)] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < CW_PER_LANE; ++u) {
+                    const int q = q0 + lane + 32 * u;
+                    if (q < Q.tot) rp[u] = pos[rj[u]];
+                }
+            };
+            auto store_regs = [&](const CwRow& Q, int q0, int buf) {
+#pragma unroll
+                for (int u = 0; u < CW_PER_LANE; ++u) {
+                    const int q = lane + 32 * u;
+                    if (q0 + q < Q.tot) {
+                        s_p[wl][buf][q] = rp[u];
+                        s_j[wl][buf][q] = rj[u];
+                    }
+                }
+            };
+            auto test_row = [&](const CwRow& Q, int q0, int buf, int rr) {
+                const int oy = rr % 3 - 1, oz = rr / 3 - 1;
+                const float offy = float(oy) * w1, offz = float(oz) * w2;
+                const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
+                const int qend = min(Q.tot, q0 + CW_ROW);
+                int seg_end = 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int seg_beg = seg_end;
+                    seg_end += Q.n[k];
+                    const int lo = max(seg_beg, q0), hi = min(seg_end, qend);
+                    const float offx = float(k - 1) * w0;
+                    const uint32_t code = codeyz | uint32_t(k);
+                    for (int q = lo; q < hi; ++q) {
+                        const float4 pj = s_p[wl][buf][q - q0];
+                        const int j = s_j[wl][buf][q - q0];
+                        const float dx = __fadd_rn(__fsub_rn(pj.x, pi.x), offx);
+                        const float dy = __fadd_rn(__fsub_rn(pj.y, pi.y), offy);
+                        const float dz = __fadd_rn(__fsub_rn(pj.z, pi.z), offz);
+                        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                        if (have && r2 < rl2 && j != i) {
+                            if (m < S.cap) {
+                                *wp = (uint32_t(j) << IDX_SHIFT) | code;
+                                wp += S.nslots;
+                            }
+                            ++m;
+                        }
+                    }
+                }
+            };
+            // software pipeline over the rows: stage row rr+1 while testing row rr
+            int buf = 0;
+            row_of(0, cur_row);
+            load_regs(cur_row, 0);
+            store_regs(cur_row, 0, buf);
+            __syncwarp();
+            for (int rr = 0; rr < 9; ++rr) {
+                // rows longer than the staging buffer are walked in chunks without overlap
+                for (int q0 = CW_ROW; q0 < cur_row.tot; q0 += CW_ROW) {
+                    test_row(cur_row, q0 - CW_ROW, buf, rr);
+                    __syncwarp();
+                    load_regs(cur_row, q0);
+                    store_regs(cur_row, q0, buf);
+                    __syncwarp();
+                }
+                const int qlast = (cur_row.tot > 0) ? ((cur_row.tot - 1) / CW_ROW) * CW_ROW : 0;
+                if (rr + 1 < 9) {
+                    row_of(rr + 1, nxt_row);
+                    load_regs(nxt_row, 0);
+                }
+                test_row(cur_row, qlast, buf, rr);
+                if (rr + 1 < 9) {
+                    store_regs(nxt_row, 0, buf ^ 1);
+                    __syncwarp();
+                    buf ^= 1;
+                    cur_row = nxt_row;
+                }
+            }
+            __syncwarp();
+            if (have) {
+                A.nbr_count[i] = m;
+                if (S.rule == MD_REBUILD_DISP) A.xref[i] = make_float4(pi.x, pi.y, pi.z, 0.0f);
+                if (m > S.cap) {
+                    atomicOr(&A.g->err, ERR_NBR_OVERFLOW);
+                    atomicMax(&A.g->max_nbr_seen, m);
+                }
+                run_sum += m;
+                run_max = max(run_max, m);
+            }
+        }
+    }
+    if (run_r >= 0) {
+        const long long ws = warp_sum_ll(run_sum);
+        const int wm = warp_max_i(run_max);
+        if (lane == 0) {
+            if (ws) atomicAdd(reinterpret_cast<unsigned long long*>(&A.rs[run_r].sum_nbrs), static_cast<unsigned long long>(ws));
+            if (wm > 0) atomicMax(&A.rs[run_r].max_nbrs, wm);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // bookkeeping after a rebuild
 // ------------------------------------------------------------------------------------------
-__global__ void k_rebuild_finish(Arrays A, Scal S)
+__global__ void k_rebuild_finish(Arrays A, Scal S, int in_graph)
 {
     if (!A.g->any_rebuild) return;
     for (int r = threadIdx.x; r < S.nrep; r += blockDim.x) {
@@ -536,6 +800,7 @@ __global__ void k_rebuild_finish(Arrays A, Scal S)
     if (threadIdx.x == 0) {
         A.g->any_rebuild = 0;
         A.g->any_reorder = 0;
+        if (in_graph) A.g->graph_rebuilds += 1;
     }
 }
 
@@ -570,6 +835,7 @@ cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L
 cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set)
 {
     const int g = tile_grid(S, L);
+    k_rebuild_list<<<1, 1024, 0, L.stream>>>(A, S);
     if (S.mode == MD_FP64) k_bin<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
     else if (S.mode == MD_MIXED) k_bin<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
     else k_bin<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
@@ -609,10 +875,11 @@ cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, i
 {
     const int g = tile_grid(S, L);
     if (S.mode == MD_FP64) k_build<double, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (L.build_batch >= 32) k_build_cw<<<std::max(1, L.grid), TILE, 0, L.stream>>>(A, S, cur);
     else if (L.build_batch >= 4) k_build<float, 4><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else if (L.build_batch >= 2) k_build<float, 2><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else k_build<float, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S);
+    k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S, L.in_graph);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ import torch
 
 CTAS = (4, 8, 12, 16)
 NBR_BATCH = (1, 2, 4)
-BUILD_BATCH = (1, 2, 4)
+BUILD_BATCH = (1, 2, 4, 32)
 
 
 def signature(system) -> str:

@@ -77,10 +77,13 @@ def test_cells_bit_exact(name, prec):
     assert np.array_equal(s.cells(), cell)
 
 
+@pytest.mark.parametrize("build", [2, 32])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", CASES)
-def test_neighbour_sets_bit_exact(name, prec):
+def test_neighbour_sets_bit_exact(name, prec, build):
     s, x, v, box, rc, skin = make(name, prec)
+    s.set_tuning(build_batch=build)
+    s.build_neighbours()
     counts, nb = s.neighbours()
     _, oc, off, onb = oracle.neighbours(x, box, rc, skin, fp32=(prec != "fp64"))
     assert np.array_equal(counts, oc)
@@ -157,7 +160,7 @@ def test_launch_shapes_do_not_change_results():
     ref, *_ = make("wca1372", "mixed")
     ref.integrate(64)
     xr, vr, _ = ref.state()
-    for ctas, nb, bb in ((4, 1, 1), (8, 4, 4), (16, 2, 2), (12, 1, 4)):
+    for ctas, nb, bb in ((4, 1, 1), (8, 4, 4), (16, 2, 2), (12, 1, 4), (8, 2, 32)):
         s, *_ = make("wca1372", "mixed")
         s.set_tuning(ctas_per_sm=ctas, nbr_batch=nb, build_batch=bb)
         s.integrate(64)
