@@ -146,11 +146,19 @@ int md_integrate(md_system* s, int32_t nsteps);
  * (out must hold md_nrep(s) entries; host pointer).  Waits for the stream. */
 int md_reduce_props(md_system* s, md_props* out);
 
-/* Time series written by md_integrate when props_every > 0: up to max_rows rows of
- * [step, U, K, W, P, px, py, pz, vmax] (9 doubles) per replica, replica-major, oldest first.
- * Returns the number of rows written per replica through *rows.  Host pointer.  Waits. */
+/* Time series written by md_integrate when props_every > 0 (a ring of the last 1024 rows): up to
+ * max_rows of the most recent rows of [step, U, K, W, P, px, py, pz, vmax] (9 doubles) per
+ * replica, replica-major, oldest first.  Returns the number of rows written per replica through
+ * *rows.  Host pointer.  Waits. */
 int md_get_series(md_system* s, double* out, int32_t max_rows, int32_t* rows);
 int md_clear_series(md_system* s);
+
+/* Queue (without waiting) a copy of the most recent time-series row of every replica,
+ * [nrep][9] doubles as in md_get_series, to dst (pinned host or device memory; pageable host
+ * memory makes the copy synchronous).  The row is the props of the last props step issued by
+ * md_integrate: the energies of that step's positions and integer-step velocities.  Errors with
+ * MD_ERR_INVALID_ARG if no props step has been issued. */
+int md_props_latest(md_system* s, double* dst);
 
 /* State in id order.  x: positions wrapped into the box; v: velocities at the current integer
  * step; f: forces at the current positions (computed by this call).  Each may be NULL; host or

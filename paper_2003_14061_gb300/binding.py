@@ -27,7 +27,7 @@ EXPORTS = (
     "md_clear_series", "md_get_state", "md_set_state", "md_get_cells", "md_get_neighbours", "md_check",
     "md_nrep", "md_natoms", "md_nbr_capacity", "md_cells_per_axis", "md_set_tuning", "md_get_tuning",
     "md_destroy", "md_last_error", "md_set_timing", "md_get_timing", "md_forces_static",
-    "md_adjoint_workspace_bytes", "md_adjoint",
+    "md_adjoint_workspace_bytes", "md_adjoint", "md_props_latest",
 )
 NPHASE = 6
 PHASES = ("step", "bin", "reorder", "build", "props", "other")
@@ -117,6 +117,7 @@ def lib(build_if_missing: bool = True):
             "md_forces_static": (ctypes.c_int, [P, i64, vp, vp, vp, vp]),
             "md_adjoint_workspace_bytes": (sz, [vp, i32, i32]),
             "md_adjoint": (ctypes.c_int, [vp, vp, sz, i32, i32, vp, vp, vp, vp]),
+            "md_props_latest": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -229,21 +229,26 @@ struct md_system {
 
     // CUDA graphs of GRAPH_STEPS steps each (one per starting position buffer)
     static constexpr int GRAPH_STEPS = 16;
+    struct GraphEntry {
+        int cur0, steps;
+        uint32_t props_mask;
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    int64_t host_series_rows = 0;     // series rows issued (props steps since creation/clear)
     cudaStream_t aux = nullptr;       // captures the IF-node bodies
     cudaStream_t gstream = nullptr;   // captures and replays the graphs (the caller's stream may be
                                       // the legacy default stream, which cannot be captured)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
 
     void drop_graphs()
     {
-        for (int b = 0; b < 2; ++b) {
-            if (gexec[b]) cudaGraphExecDestroy(gexec[b]);
-            if (graph[b]) cudaGraphDestroy(graph[b]);
-            gexec[b] = nullptr;
-            graph[b] = nullptr;
+        for (auto& g : graphs) {
+            cudaGraphExecDestroy(g.exec);
+            cudaGraphDestroy(g.graph);
         }
+        graphs.clear();
     }
 
     cudaEvent_t take_event()
@@ -400,15 +405,16 @@ int load_state(md_system* s, const double* x, const double* v)
     GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, 1));
     GBMD_CUDA(launch_rebuild(s->A, s->S, s->L, s->cur, true));
     s->host_step = 0;
+    s->host_series_rows = 0;
     s->binned_fresh = false;
     return MD_OK;
 }
 
-// Capture GRAPH_STEPS steps starting from position buffer cur0: each step is the fused step
-// kernel followed by an IF node whose body is the rebuild sequence; the step kernel opens the IF
-// node only when some replica's refresh criterion fired, so steps without a rebuild launch
-// nothing but the step kernel.
-int capture_graph(md_system* s, int cur0)
+// Capture `steps` steps starting from position buffer cur0 (bit j of props_mask: step j also
+// reduces the props into the time series).  Each step is the fused step kernel followed by an
+// IF node whose body is the rebuild sequence; the step kernel opens the IF node only when some
+// replica's refresh criterion fired, so steps without a rebuild launch nothing else.
+int capture_graph(md_system* s, int cur0, int steps, uint32_t props_mask, cudaGraphExec_t* out_exec)
 {
     if (!s->aux) GBMD_CUDA(cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
     if (!s->gstream) GBMD_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
@@ -418,7 +424,7 @@ int capture_graph(md_system* s, int cur0)
     GBMD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaError_t err = cudaSuccess;
     int cur = cur0;
-    for (int k = 0; k < md_system::GRAPH_STEPS && err == cudaSuccess; ++k) {
+    for (int k = 0; k < steps && err == cudaSuccess; ++k) {
         cudaStreamCaptureStatus cs;
         cudaGraph_t g = nullptr;
         const cudaGraphNode_t* deps = nullptr;
@@ -431,7 +437,7 @@ int capture_graph(md_system* s, int cur0)
         L.stream = st;
         L.cond = h;
         L.use_cond = 1;
-        if (err == cudaSuccess) err = launch_step(s->A, s->S, L, cur, false);
+        if (err == cudaSuccess) err = launch_step(s->A, s->S, L, cur, (props_mask >> k) & 1u);
         cur ^= 1;
         if (err == cudaSuccess) err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
         cudaGraphNodeParams cp = {};
@@ -473,8 +479,8 @@ int capture_graph(md_system* s, int cur0)
         cudaGraphDestroy(graph);
         return fail(MD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
     }
-    s->graph[cur0] = graph;
-    s->gexec[cur0] = exec;
+    s->graphs.push_back({cur0, steps, props_mask, graph, exec});
+    *out_exec = exec;
     return MD_OK;
 }
 
@@ -613,26 +619,37 @@ int md_integrate(md_system* s, int32_t nsteps)
         s->binned_fresh = false;
     }
     int32_t k = 0;
-    if (s->tune.use_graph == 1 && s->p.props_every == 0) {
-        const int G = md_system::GRAPH_STEPS;
-        while (k + G <= nsteps) {
-            if (!s->gexec[s->cur]) {
-                const int rc = capture_graph(s, s->cur);
+    if (s->tune.use_graph == 1) {
+        // replay cached graphs of 16 steps, or of 1 step for the remainder; a graph is keyed by
+        // its starting buffer, length and which of its steps reduce the props
+        while (k < nsteps) {
+            const int G = (nsteps - k >= md_system::GRAPH_STEPS) ? md_system::GRAPH_STEPS : 1;
+            uint32_t mask = 0;
+            for (int j = 0; j < G; ++j)
+                if (s->p.props_every > 0 && ((s->host_step + j) % s->p.props_every == 0)) mask |= 1u << j;
+            cudaGraphExec_t exec = nullptr;
+            for (auto& g : s->graphs)
+                if (g.cur0 == s->cur && g.steps == G && g.props_mask == mask) exec = g.exec;
+            if (!exec) {
+                const int rc = capture_graph(s, s->cur, G, mask, &exec);
                 if (rc) return rc;
             }
-            Phase t(s, MD_PHASE_STEP, G);
+            Phase t(s, MD_PHASE_STEP, G + 2 * __builtin_popcount(mask));
             // replay on the library's stream, ordered after and before the caller's stream
             GBMD_CUDA(cudaEventRecord(s->ev_in, s->L.stream));
             GBMD_CUDA(cudaStreamWaitEvent(s->gstream, s->ev_in, 0));
-            GBMD_CUDA(cudaGraphLaunch(s->gexec[s->cur], s->gstream));
+            GBMD_CUDA(cudaGraphLaunch(exec, s->gstream));
             GBMD_CUDA(cudaEventRecord(s->ev_out, s->gstream));
             GBMD_CUDA(cudaStreamWaitEvent(s->L.stream, s->ev_out, 0));
             k += G;
             s->host_step += G;
+            s->host_series_rows += __builtin_popcount(mask);
+            if (G & 1) s->cur ^= 1;
         }
     }
     for (; k < nsteps; ++k) {
         const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
+        if (props) s->host_series_rows += 1;
         {
             Phase t(s, MD_PHASE_STEP, props ? 3 : 1);
             GBMD_CUDA(launch_step(s->A, s->S, s->L, s->cur, props));
@@ -707,17 +724,17 @@ int md_reduce_props(md_system* s, md_props* out)
 int md_get_series(md_system* s, double* out, int32_t max_rows, int32_t* rows)
 {
     if (!s || !out || !rows || max_rows < 0) return fail(MD_ERR_INVALID_ARG, "bad arguments");
-    std::vector<RepState> st(s->plan.nrep);
-    GBMD_CUDA(cudaMemcpyAsync(st.data(), s->A.rs, sizeof(RepState) * st.size(), cudaMemcpyDeviceToHost,
-                              s->L.stream));
     GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
-    int32_t nr = 0;
-    for (auto& x : st) nr = std::max(nr, x.series_rows);
-    nr = std::min(nr, max_rows);
-    for (int32_t r = 0; r < s->plan.nrep; ++r) {
-        GBMD_CUDA(cudaMemcpyAsync(out + size_t(r) * max_rows * SERIES_COLS,
-                                  s->A.series + size_t(r) * s->plan.series_cap * SERIES_COLS,
-                                  sizeof(double) * SERIES_COLS * nr, cudaMemcpyDeviceToHost, s->L.stream));
+    const int64_t written = s->host_series_rows;
+    const int64_t cap = s->plan.series_cap;
+    const int32_t nr = int32_t(std::min<int64_t>(std::min<int64_t>(written, cap), max_rows));
+    const int nrep = s->plan.nrep;
+    // the last nr rows, oldest first: ring rows (written - nr + q) % cap, [row][replica][col]
+    for (int32_t q = 0; q < nr; ++q) {
+        const int64_t row = (written - nr + q) % cap;
+        GBMD_CUDA(cudaMemcpy2DAsync(out + size_t(q) * SERIES_COLS, sizeof(double) * SERIES_COLS * max_rows,
+                                    s->A.series + size_t(row) * nrep * SERIES_COLS, sizeof(double) * SERIES_COLS,
+                                    sizeof(double) * SERIES_COLS, nrep, cudaMemcpyDeviceToHost, s->L.stream));
     }
     *rows = nr;
     return latch_error(s);
@@ -734,6 +751,18 @@ int md_clear_series(md_system* s)
     GBMD_CUDA(cudaMemcpyAsync(s->A.rs, st.data(), sizeof(RepState) * st.size(), cudaMemcpyHostToDevice,
                               s->L.stream));
     GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    s->host_series_rows = 0;
+    return MD_OK;
+}
+
+int md_props_latest(md_system* s, double* dst)
+{
+    if (!s || !dst) return fail(MD_ERR_INVALID_ARG, "system or dst is NULL");
+    if (s->host_series_rows == 0) return fail(MD_ERR_INVALID_ARG, "no props step has been issued (props_every = 0?)");
+    const int64_t row = (s->host_series_rows - 1) % s->plan.series_cap;
+    const size_t bytes = sizeof(double) * SERIES_COLS * s->plan.nrep;
+    GBMD_CUDA(cudaMemcpyAsync(dst, s->A.series + size_t(row) * s->plan.nrep * SERIES_COLS, bytes, cudaMemcpyDefault,
+                              s->L.stream));
     return MD_OK;
 }
 

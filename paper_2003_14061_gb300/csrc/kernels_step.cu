@@ -526,13 +526,13 @@ __global__ void __launch_bounds__(32) k_props_finalize(Arrays A, Scal S, int to_
     A.props[r] = pr;
     if (to_series) {
         RepState& sw = A.rs[r];
-        const int row = sw.series_rows;
-        if (row < S.series_cap) {
-            double* o = A.series + (int64_t(r) * S.series_cap + row) * SERIES_COLS;
-            o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
-            o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
-            sw.series_rows = row + 1;
-        }
+        // ring of series_cap rows laid out [row][replica][column]: the latest row of every
+        // replica is contiguous (one copy reads it)
+        const int row = sw.series_rows % S.series_cap;
+        double* o = A.series + (int64_t(row) * S.nrep + r) * SERIES_COLS;
+        o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
+        o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
+        sw.series_rows += 1;
     }
 }
 

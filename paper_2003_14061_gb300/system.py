@@ -144,6 +144,10 @@ class MDSystem:
         self._call("md_get_series", buf.ctypes.data_as(ctypes.c_void_p), int(max_rows), ctypes.byref(rows))
         return buf[:, : rows.value]
 
+    def props_latest_into(self, dst: torch.Tensor):
+        """Queue a copy of the latest props row ([nrep, 9] float64) into dst (pinned or device)."""
+        self._call("md_props_latest", ctypes.c_void_p(dst.data_ptr()))
+
     def clear_series(self):
         self._call("md_clear_series")
 

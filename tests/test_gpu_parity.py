@@ -195,6 +195,31 @@ def test_energy_conservation_matches_oracle():
     assert abs(E[0] - Eo[0]) / n <= 1e-6
 
 
+def test_series_ring_and_latest_row():
+    s, x, v, box, rc, skin = make("wca1372", "mixed", props_every=1)
+    s.integrate(40)                                   # 2 graphs of 16 + 8 single steps
+    ser = s.series(64)[0]
+    assert ser.shape[0] == 40 and np.array_equal(ser[:, 0], np.arange(40))
+    row = torch.empty((1, 9), dtype=torch.float64).pin_memory()
+    s.props_latest_into(row)
+    torch.cuda.synchronize()
+    assert np.array_equal(row.numpy()[0], ser[-1])
+    s.integrate(1100)                                 # the ring keeps the last 1024 rows
+    ser = s.series(2000)[0]
+    assert ser.shape[0] == 1024 and ser[-1, 0] == 1139 and ser[0, 0] == 1139 - 1023
+    # the fused per-step props equal a separate reduction at the same state
+    d = make("wca1372", "mixed", props_every=1)[0]
+    d.set_tuning(use_graph=2)
+    d.integrate(10)
+    r9 = d.series(16)[0][-1]                          # props of step 9 (before its drift)
+    e = make("wca1372", "mixed")[0]
+    e.set_tuning(use_graph=2)
+    e.integrate(9)
+    p = e.props()[0]
+    assert p["step"] == 9
+    assert abs(r9[1] - p["U"]) <= 1e-9 * abs(p["U"]) and abs(r9[2] - p["K"]) <= 1e-9 * abs(p["K"])
+
+
 def test_rebuild_rules():
     for rule in ("vmax", "disp", "every"):
         s, x, v, box, rc, skin = make("wca1372", "mixed", rebuild_rule=rule)
