@@ -41,6 +41,18 @@ DT = 0.005
 SEED = {"wca4m": 2, "lj16m": 3, "batch512": 4}
 
 
+def combine_ranks(ms: float, atoms: int, steps: int, device=None):
+    """(max time over ranks in ms, total atoms, whole-job particle-steps/s); one process per GPU."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    a = torch.tensor([float(atoms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    ms_max, total = float(t.item()), int(a.item())
+    return ms_max, total, total * steps / (ms_max * 1e-3)
+
+
 def traffic_per_atom(kernel: str):
     """DRAM bytes per atom of a kernel from its committed ncu capture, if the source is unchanged."""
     import hashlib
@@ -206,11 +218,10 @@ def run_gb300(args, rank, world, local_rank):
         launches += 11 * int(nrb)
     mean_nbrs = float(np.average([p["mean_nbrs"] for p in props], weights=s.n_rep))
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_atoms = n * world
-    value = total_atoms * args.steps / (ms * 1e-3)
+        ms, total_atoms, value = combine_ranks(ms, n, args.steps, device=dev)
+    else:
+        total_atoms = n
+        value = total_atoms * args.steps / (ms * 1e-3)
 
     # per-kernel durations: the same workload continued with direct launches, every phase
     # bracketed by CUDA events on the library's stream (graph replays cannot be split per kernel)

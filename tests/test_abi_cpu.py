@@ -75,3 +75,12 @@ def test_null_handles_fail_cleanly():
     assert L.md_reduce_props(None, None) == -1
     assert L.md_destroy(None) == -1
     assert L.md_nrep(None) == 0
+
+
+def test_slot_and_cell_limits():
+    # 2^26 atom slots: just below is accepted, just above is refused
+    p = make_params(n=(1 << 26) - 128, box=(460.0, 460.0, 460.0), skin=0.0)
+    assert B.lib().md_workspace_bytes(ctypes.byref(p)) > 0
+    p = make_params(n=(1 << 26) + 1, box=(460.0, 460.0, 460.0), skin=0.0)
+    assert B.lib().md_workspace_bytes(ctypes.byref(p)) == 0
+    assert "2^26" in B.last_error()
