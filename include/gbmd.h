@@ -192,10 +192,11 @@ typedef struct {
     int32_t ctas_per_sm;     /* persistent CTAs per SM for the tile loops (1..64); grid = SMs x this;
                                 the step kernel is also compiled to fit 4, 8, 12 or 16 CTAs per SM
                                 (the largest not above this) and its grid is capped at residency */
-    int32_t nbr_batch;       /* W entries each thread loads together in the pair loop: 1, 2 or 4 */
-    int32_t build_batch;     /* neighbour build: 1, 2 or 4 = one thread per atom loading that many
-                                candidates together; 32 = one warp per cell, candidates shared
-                                by warp shuffles (for cells of tens of atoms) */
+    int32_t nbr_batch;       /* W entries each thread loads together in the pair loop: 2, 4 or 8 */
+    int32_t build_batch;     /* neighbour build: 2 or 4 = one thread per atom loading that many
+                                candidates together; 32 = one warp per cell, each row of
+                                candidates staged once in shared memory (for cells of tens of
+                                atoms) */
     int32_t use_graph;       /* 1: md_integrate replays captured CUDA graphs; 2: direct launches */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
@@ -225,9 +226,10 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
 /* Per-phase timing (the breakdown of Table 2 of the paper: neighbour matrix, forces +
  * integration, layer/cell assignment, reorder, energy).  With timing enabled, every phase is
  * bracketed by CUDA events on the system's stream.  md_get_timing waits for the stream, then
- * returns for each phase the summed milliseconds (0 while timing is off), the number of times
- * it was issued and the number of kernels launched, and resets the counters.  Arrays hold
- * MD_NPHASE entries (host pointers, each may be NULL). */
+ * returns for each phase the summed milliseconds and the number of timed intervals they add up
+ * (both 0 while timing is off), and the number of kernels launched (counted whether or not
+ * timing is on), and resets the counters.  Arrays hold MD_NPHASE entries (host pointers, each
+ * may be NULL). */
 #define MD_NPHASE 6
 enum {
     MD_PHASE_STEP = 0,     /* F1 fused with the leapfrog update (and F2 when props_every hits) */

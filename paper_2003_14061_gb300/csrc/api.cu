@@ -166,6 +166,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.W = c.take<uint32_t>(ns * size_t(P.cap));
     if (P.rule == MD_REBUILD_DISP) a.xref = c.take<float4>(ns);
     a.perm = c.take<int32_t>(ns);
+    if (!f64) a.psort = c.take<float4>(ns);
     if (!f32) for (int q = 0; q < 3; ++q) a.tmp_d[q] = c.take<double>(ns);
     for (int q = 0; q < 3; ++q) a.tmp_v[q] = c.take<double>(ns);
     for (int q = 0; q < 2; ++q) a.tmp_i[q] = c.take<int32_t>(ns);
@@ -285,8 +286,8 @@ struct Phase {
     Phase(md_system* s_, int ph_, int nlaunch) : s(s_), ph(ph_)
     {
         s->launches[ph] += nlaunch;
-        s->calls[ph] += 1;
         if (s->timing) {
+            s->calls[ph] += 1;            // timed intervals: the divisor of the summed milliseconds
             cudaEvent_t a = s->take_event();
             b = s->take_event();
             cudaEventRecord(a, s->L.stream);
@@ -542,7 +543,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
     s->nsm = prop.multiProcessorCount;
     s->tune.ctas_per_sm = 12;
-    s->tune.nbr_batch = 2;
+    s->tune.nbr_batch = 4;
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
     apply_tuning(s);
@@ -839,10 +840,10 @@ int md_set_tuning(md_system* s, const md_tuning* t)
 {
     if (!s || !t) return fail(MD_ERR_INVALID_ARG, "bad arguments");
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(MD_ERR_INVALID_ARG, "ctas_per_sm in 0..64");
-    if (t->nbr_batch && t->nbr_batch != 1 && t->nbr_batch != 2 && t->nbr_batch != 4)
-        return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 1, 2 or 4");
-    if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
-        return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2, 4 or 32");
+    if (t->nbr_batch && t->nbr_batch != 2 && t->nbr_batch != 4 && t->nbr_batch != 8)
+        return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 2, 4 or 8");
+    if (t->build_batch && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
+        return fail(MD_ERR_INVALID_ARG, "build_batch must be 2, 4 or 32");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;

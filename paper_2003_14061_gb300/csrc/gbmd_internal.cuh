@@ -95,6 +95,7 @@ struct Arrays {
     uint32_t* W;
     float4* xref;             // positions at the last rebuild (rule DISP)
     int32_t* perm;            // cell-ordered slots (the matrix H of Sec. 2.3, flattened)
+    float4* psort;            // FP32 positions in cell order, slot in .w (MD_MIXED, MD_FP32)
     // reorder scratch, per slot
     double* tmp_d[3];
     double* tmp_v[3];

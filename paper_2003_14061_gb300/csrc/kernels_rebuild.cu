@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(TILE) k_scatter(Arrays A, Scal S)
     }
 }
 
-__global__ void __launch_bounds__(256) k_sort_cells(Arrays A, Scal S)
+__global__ void __launch_bounds__(256) k_sort_cells(Arrays A, Scal S, int cur)
 {
     if (!A.g->any_rebuild) return;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < S.ncells;
@@ -354,6 +354,15 @@ __global__ void __launch_bounds__(256) k_sort_cells(Arrays A, Scal S)
                 --q;
             }
             A.perm[q + 1] = key;
+        }
+        // the cell-ordered copy of the FP32 positions read by the neighbour build, slot in .w
+        if (A.psort && A.rs[A.cell_rep[c]].rebuild) {
+            const float4* __restrict__ pos = A.pos32[cur];
+            for (int k = b; k < e; ++k) {
+                const int32_t j = A.perm[k];
+                const float4 p = pos[j];
+                A.psort[k] = make_float4(p.x, p.y, p.z, __int_as_float(j));
+            }
         }
     }
 }
@@ -417,7 +426,9 @@ __global__ void __launch_bounds__(TILE) k_reorder_copy(Arrays A, Scal S, int cur
         }
         A.id[slot] = A.tmp_i[0][slot];
         A.cell[slot] = A.tmp_i[1][slot];
-        A.perm[A.cstart[R.cell0] + j] = int32_t(slot);
+        const int k = A.cstart[R.cell0] + int(j);
+        A.perm[k] = int32_t(slot);
+        if (MODE != MD_FP64) reinterpret_cast<float*>(A.psort + k)[3] = __int_as_float(int(slot));
     }
 }
 
@@ -588,6 +599,134 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
 }
 
 
+// N5 in FP32 from the cell-ordered copy of the positions: psort[k] is the k-th atom of the cell
+// order (the order of perm) with its slot in .w, so the candidates of a 3-cell row are one
+// contiguous run of psort (three separate runs at a periodic wrap in x), read in order with no
+// load through perm.  x and y of a candidate are adjacent in its float4 and go through packed
+// FP32x2 adds; each lane rounds as the scalar criterion does (a - b is a + (-b)), and the rows,
+// cells and candidates are visited in k_build's order, so W is entry for entry k_build's.
+__device__ __forceinline__ void nbr_test(const float4& p, const float2& npxy, float npz, float offx, float offy,
+                                         float offz, bool valid, uint32_t code, int me, float rl2, uint32_t*& wp,
+                                         int& m, int cap, int64_t nslots)
+{
+    const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(p.x, p.y), npxy), make_float2(offx, offy));
+    const float dz = __fadd_rn(__fadd_rn(p.z, npz), offz);
+    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dxy.y, dxy.y, __fmul_rn(dxy.x, dxy.x)));
+    const int j = __float_as_int(p.w);
+    if (valid && r2 < rl2 && j != me) {
+        if (m < cap) {
+            *wp = (uint32_t(j) << IDX_SHIFT) | code;
+            wp += nslots;
+        }
+        ++m;
+    }
+}
+
+template <int BB>
+__global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_rebuild) return;
+    const float4* __restrict__ pos = A.pos32[cur];
+    const float4* __restrict__ ps = A.psort;
+    const int32_t* __restrict__ cs = A.cstart;
+    const float rl2 = S.rl2f;
+    const float skip2 = rl2 * (1.0f + 1e-5f);
+    const int nrb = A.g->n_rb_tiles;
+    const int per = (nrb + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(nrb, t_begin + per);
+    int run_r = -1, run_max = 0;
+    long long run_sum = 0;
+    for (int it = t_begin; it < t_end; ++it) {
+        const int t = A.rb_tiles[it];
+        const int r = A.tile_rep[t];
+        if (r != run_r) {
+            if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
+            run_r = r;
+            run_sum = 0;
+            run_max = 0;
+        }
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const bool active = slot - R.slot0 < R.n;
+        int m = 0;
+        if (active) {
+            const float4 pi = pos[slot];
+            int cx, cy, cz;
+            unpack_cell(__float_as_uint(pi.w), cx, cy, cz);
+            const float w0 = R.wf[0], w1 = R.wf[1], w2 = R.wf[2];
+            const int ncx = R.nc[0];
+            const bool inner = cx > 0 && cx < ncx - 1;
+            const int me = int(slot);
+            uint32_t* wp = A.W + slot;
+            // neighbouring cells whose nearest point is beyond r_c + skin are skipped (as k_build)
+            const float dlo2[3] = {pi.x * pi.x, pi.y * pi.y, pi.z * pi.z};
+            const float dhi2[3] = {(w0 - pi.x) * (w0 - pi.x), (w1 - pi.y) * (w1 - pi.y), (w2 - pi.z) * (w2 - pi.z)};
+            const float2 npxy = make_float2(-pi.x, -pi.y);
+            const float npz = -pi.z;
+            for (int oz = -1; oz <= 1; ++oz) {
+                int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
+                const float offz = float(oz) * w2;
+                for (int oy = -1; oy <= 1; ++oy) {
+                    int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
+                    const float offy = float(oy) * w1;
+                    const float dyz = ((oy < 0) ? dlo2[1] : ((oy > 0) ? dhi2[1] : 0.0f)) +
+                                      ((oz < 0) ? dlo2[2] : ((oz > 0) ? dhi2[2] : 0.0f));
+                    if (dyz > skip2) continue;
+                    const bool use_l = dyz + dlo2[0] <= skip2, use_r = dyz + dhi2[0] <= skip2;
+                    const int row = R.cell0 + (nz * R.nc[1] + ny) * ncx;
+                    const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
+                    if (inner) {
+                        // cells cx-1, cx, cx+1 are adjacent runs [b0,b1) [b1,b2) [b2,b3) of psort
+                        const int b0 = cs[row + cx - 1], b1 = cs[row + cx], b2 = cs[row + cx + 1];
+                        const int kb = use_l ? b0 : b1;
+                        const int ke = use_r ? cs[row + cx + 2] : b2;
+                        for (int k0 = kb; k0 < ke; k0 += BB) {
+                            float4 pj[BB];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) pj[u] = ps[min(k0 + u, ke - 1)];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) {
+                                const int k = k0 + u;
+                                const uint32_t c = uint32_t(k >= b1) + uint32_t(k >= b2);   // o_x + 1
+                                const float offx = (k < b1) ? -w0 : ((k < b2) ? 0.0f : w0);
+                                nbr_test(pj[u], npxy, npz, offx, offy, offz, k < ke, codeyz | c, me, rl2, wp, m,
+                                         S.cap, S.nslots);
+                            }
+                        }
+                    } else {
+                        // a periodic wrap in x: the three cells are separate runs, in the same order
+                        const int xs[3] = {(cx == 0) ? ncx - 1 : cx - 1, cx, (cx == ncx - 1) ? 0 : cx + 1};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if ((c == 0 && !use_l) || (c == 2 && !use_r)) continue;
+                            const int b = cs[row + xs[c]], e = cs[row + xs[c] + 1];
+                            const float offx = float(c - 1) * w0;
+                            for (int k0 = b; k0 < e; k0 += BB) {
+                                float4 pj[BB];
+#pragma unroll
+                                for (int u = 0; u < BB; ++u) pj[u] = ps[min(k0 + u, e - 1)];
+#pragma unroll
+                                for (int u = 0; u < BB; ++u)
+                                    nbr_test(pj[u], npxy, npz, offx, offy, offz, k0 + u < e, codeyz | uint32_t(c), me,
+                                             rl2, wp, m, S.cap, S.nslots);
+                            }
+                        }
+                    }
+                }
+            }
+            A.nbr_count[slot] = m;
+            if (S.rule == MD_REBUILD_DISP) A.xref[slot] = make_float4(pi.x, pi.y, pi.z, 0.0f);
+            if (m > S.cap) {
+                atomicOr(&A.g->err, ERR_NBR_OVERFLOW);
+                atomicMax(&A.g->max_nbr_seen, m);
+            }
+            run_sum += m;
+            run_max = max(run_max, m);
+        }
+    }
+    if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
+}
+
 // ------------------------------------------------------------------------------------------
 // N5 for dense cells (tens of atoms per cell, e.g. the LJ liquid at r_c + skin = 2.8): one warp
 // per cell, one lane per atom of it.  The candidates of each 3-cell row of the 27-cell
@@ -616,7 +755,7 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
     if (!A.g->any_rebuild) return;
     __shared__ float4 s_p[CW_WARPS][2][CW_ROW];
     __shared__ int32_t s_j[CW_WARPS][2][CW_ROW];
-    const float4* __restrict__ pos = A.pos32[cur];
+    const float4* __restrict__ ps = A.psort;
     const float rl2 = S.rl2f;
     const float skip2 = rl2 * (1.0f + 1e-5f);
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -651,8 +790,8 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
         const int ab = A.cstart[c], ae = A.cstart[c + 1];
         for (int a0 = ab; a0 < ae; a0 += 32) {
             const bool have = a0 + lane < ae;
-            const int i = have ? A.perm[a0 + lane] : -1;
-            const float4 pi = have ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 pi = have ? ps[a0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int i = have ? __float_as_int(pi.w) : -1;
             const float dl[3] = {pi.x * pi.x, pi.y * pi.y, pi.z * pi.z};
             const float dh[3] = {(w0 - pi.x) * (w0 - pi.x), (w1 - pi.y) * (w1 - pi.y), (w2 - pi.z) * (w2 - pi.z)};
             int m = 0;
@@ -682,12 +821,10 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
 #pragma unroll
                 for (int u = 0; u < CW_PER_LANE; ++u) {
                     const int q = q0 + lane + 32 * u;
-                    rj[u] = (q < Q.tot) ? A.perm[cw_index(Q, q)] : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < CW_PER_LANE; ++u) {
-                    const int q = q0 + lane + 32 * u;
-                    if (q < Q.tot) rp[u] = pos[rj[u]];
+                    if (q < Q.tot) {
+                        rp[u] = ps[cw_index(Q, q)];
+                        rj[u] = __float_as_int(rp[u].w);
+                    }
                 }
             };
             auto store_regs = [&](const CwRow& Q, int q0, int buf) {
@@ -844,7 +981,7 @@ cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, in
     k_scan_apply<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
     k_scatter<<<g, TILE, 0, L.stream>>>(A, S);
     const int gs = int(std::min<int64_t>((S.ncells + 255) / 256, int64_t(L.grid) * 8));
-    k_sort_cells<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S);
+    k_sort_cells<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S, cur);
     return cudaGetLastError();
 }
 
@@ -876,9 +1013,8 @@ cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, i
     const int g = tile_grid(S, L);
     if (S.mode == MD_FP64) k_build<double, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else if (L.build_batch >= 32) k_build_cw<<<std::max(1, L.grid), TILE, 0, L.stream>>>(A, S, cur);
-    else if (L.build_batch >= 4) k_build<float, 4><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    else if (L.build_batch >= 2) k_build<float, 2><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    else k_build<float, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (L.build_batch >= 4) k_build_sorted<4><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else k_build_sorted<2><<<g, TILE, 0, L.stream>>>(A, S, cur);
     k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S, L.in_graph);
     return cudaGetLastError();
 }

@@ -20,11 +20,12 @@
 namespace gbmd {
 
 // Periodic offsets of a W entry as exact floats without conversion ops: OR-ing the code bits into
-// the mantissa of 2^23 gives 2^23 + code; subtracting 2^23 + (the code of offset 0) leaves
-// o_x, 4 o_y and 16 o_z, which multiply w_x, w_y / 4 and w_z / 16 (exact power-of-two scalings).
-__device__ __forceinline__ float offx_f(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 3u)) - 8388609.0f; }
-__device__ __forceinline__ float offy4_f(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 12u)) - 8388612.0f; }
-__device__ __forceinline__ float offz16_f(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 48u)) - 8388624.0f; }
+// the mantissa of 2^23 gives 2^23 + code (the *_raw values); subtracting 2^23 + (the code of
+// offset 0) leaves o_x, 4 o_y and 16 o_z, which multiply w_x, w_y / 4 and w_z / 16 (exact
+// power-of-two scalings).
+__device__ __forceinline__ float offx_raw(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 3u)); }
+__device__ __forceinline__ float offy_raw(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 12u)); }
+__device__ __forceinline__ float offz_raw(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 48u)); }
 
 // reciprocal to ~1 ulp (the force tolerance is 1e-5 relative)
 __device__ __forceinline__ float rcp_approx(float x)
@@ -40,46 +41,69 @@ __device__ __forceinline__ float rcp_approx(float x)
 struct AccF { float fx, fy, fz, u, w; };
 struct AccD { double fx, fy, fz, u, w; };
 
-// One thread per atom over its column of W, NB entries at a time: the NB row loads are issued
-// together, then the NB position gathers, so each thread keeps 2 NB loads in flight.
+// One thread per atom over its column of W, NB entries at a time.  The row loads of batch b+1 are
+// issued together with the position gathers of batch b, so each thread keeps 2 NB loads in flight
+// and a batch waits for one memory latency, not two.  The arithmetic runs on packed FP32x2
+// operations (one instruction for two lanes, each lane rounded as the scalar operation): entries
+// 2k and 2k+1 of the column go to lanes x and y, and the two lanes' sums are added at the end, so
+// the summation order is the same for every NB.
 template <int NB>
 __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const Rep& R,
                                           const float4* __restrict__ pos, int64_t slot, float4 pi)
 {
-    AccF a{0.f, 0.f, 0.f, 0.f, 0.f};
+    static_assert(NB % 2 == 0, "W entries are processed in pairs");
     const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
     const uint32_t* __restrict__ Wc = A.W + slot;
-    const float wx = R.wf[0], wy4 = 0.25f * R.wf[1], wz16 = 0.0625f * R.wf[2];
-    for (int m0 = 0; m0 < mm; m0 += NB) {
-        uint32_t e[NB];
+    const float2 wx = make_float2(R.wf[0], R.wf[0]);
+    const float2 wy4 = make_float2(0.25f * R.wf[1], 0.25f * R.wf[1]);
+    const float2 wz16 = make_float2(0.0625f * R.wf[2], 0.0625f * R.wf[2]);
+    const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
+    const float2 sig2 = make_float2(S.sig2f, S.sig2f), eps48 = make_float2(S.eps48f, S.eps48f);
+    float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, u = fx, w = fx;
+    uint32_t e[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            e[k] = (m0 + k < mm) ? __ldcs(Wc + int64_t(m0 + k) * S.nslots) : 0u;
+    for (int k = 0; k < NB; ++k) e[k] = (k < mm) ? __ldcs(Wc + int64_t(k) * S.nslots) : 0u;
+    for (int m0 = 0; m0 < mm; m0 += NB) {
         float4 pj[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] >> IDX_SHIFT)) : pi;
+        for (int k = 0; k < NB; ++k) pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] >> IDX_SHIFT)) : pi;
+        uint32_t en[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            const uint32_t ek = e[k];
-            const float dx = fmaf(offx_f(ek), wx, pj[k].x - pi.x);
-            const float dy = fmaf(offy4_f(ek), wy4, pj[k].y - pi.y);
-            const float dz = fmaf(offz16_f(ek), wz16, pj[k].z - pi.z);
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (m0 + k < mm && r2 < S.rc2f) {
-                const float ri2 = rcp_approx(r2);
-                const float sr2 = S.sig2f * ri2;
-                const float sr6 = sr2 * sr2 * sr2;
-                const float fs = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;   // g(r^2)
-                a.fx = fmaf(-fs, dx, a.fx);                              // f_i = g (x_i - x_j)
-                a.fy = fmaf(-fs, dy, a.fy);
-                a.fz = fmaf(-fs, dz, a.fz);
-                a.u += fmaf(S.eps4f * sr6, sr6 - 1.0f, -S.ucf);
-                a.w = fmaf(fs, r2, a.w);
-            }
+        for (int k = 0; k < NB; ++k)
+            en[k] = (m0 + NB + k < mm) ? __ldcs(Wc + int64_t(m0 + NB + k) * S.nslots) : 0u;
+#pragma unroll
+        for (int k = 0; k < NB; k += 2) {
+            const uint32_t e0 = e[k], e1 = e[k + 1];
+            const float2 ox = __fadd2_rn(make_float2(offx_raw(e0), offx_raw(e1)), make_float2(-8388609.0f, -8388609.0f));
+            const float2 oy = __fadd2_rn(make_float2(offy_raw(e0), offy_raw(e1)), make_float2(-8388612.0f, -8388612.0f));
+            const float2 oz = __fadd2_rn(make_float2(offz_raw(e0), offz_raw(e1)), make_float2(-8388624.0f, -8388624.0f));
+            const float2 dx = __ffma2_rn(ox, wx, __fadd2_rn(make_float2(pj[k].x, pj[k + 1].x), npx));
+            const float2 dy = __ffma2_rn(oy, wy4, __fadd2_rn(make_float2(pj[k].y, pj[k + 1].y), npy));
+            const float2 dz = __ffma2_rn(oz, wz16, __fadd2_rn(make_float2(pj[k].z, pj[k + 1].z), npz));
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const bool in0 = (m0 + k < mm) && r2.x < S.rc2f;
+            const bool in1 = (m0 + k + 1 < mm) && r2.y < S.rc2f;
+            const float2 ri2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+            const float2 sr2 = __fmul2_rn(sig2, ri2);
+            const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+            float2 fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(eps48, sr6), __fadd2_rn(sr6, make_float2(-0.5f, -0.5f))), ri2);
+            fs.x = in0 ? fs.x : 0.0f;                                      // g(r^2), zero outside r_c
+            fs.y = in1 ? fs.y : 0.0f;
+            fx = __ffma2_rn(fs, dx, fx);                                   // sum g (x_j - x_i)
+            fy = __ffma2_rn(fs, dy, fy);
+            fz = __ffma2_rn(fs, dz, fz);
+            float2 ut = __ffma2_rn(__fmul2_rn(make_float2(S.eps4f, S.eps4f), sr6),
+                                   __fadd2_rn(sr6, make_float2(-1.0f, -1.0f)), make_float2(-S.ucf, -S.ucf));
+            ut.x = in0 ? ut.x : 0.0f;
+            ut.y = in1 ? ut.y : 0.0f;
+            u = __fadd2_rn(u, ut);
+            w = __ffma2_rn(fs, r2, w);
         }
+#pragma unroll
+        for (int k = 0; k < NB; ++k) e[k] = en[k];
     }
-    return a;
+    // f_i = sum g (x_i - x_j) = -(sum g (x_j - x_i))
+    return AccF{-(fx.x + fx.y), -(fy.x + fy.y), -(fz.x + fz.y), u.x + u.y, w.x + w.y};
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p)
@@ -668,13 +692,13 @@ static int minb_of(int ctas_per_sm)
 #define GBMD_DISPATCH_NB_MINB(M, FN)                                                      \
     {                                                                                     \
         const int mb = minb_of(L.ctas_req);                                               \
-        const int nb = L.nbr_batch >= 4 ? 4 : L.nbr_batch >= 2 ? 2 : 1;                    \
-        if (nb == 4) {                                                                    \
+        const int nb = L.nbr_batch >= 8 ? 8 : L.nbr_batch >= 4 ? 4 : 2;                    \
+        if (nb == 8) {                                                                    \
+            if (mb == 16) FN(M, 8, 16) else if (mb == 12) FN(M, 8, 12) else if (mb == 8) FN(M, 8, 8) else FN(M, 8, 4) \
+        } else if (nb == 4) {                                                             \
             if (mb == 16) FN(M, 4, 16) else if (mb == 12) FN(M, 4, 12) else if (mb == 8) FN(M, 4, 8) else FN(M, 4, 4) \
-        } else if (nb == 2) {                                                             \
-            if (mb == 16) FN(M, 2, 16) else if (mb == 12) FN(M, 2, 12) else if (mb == 8) FN(M, 2, 8) else FN(M, 2, 4) \
         } else {                                                                          \
-            if (mb == 16) FN(M, 1, 16) else if (mb == 12) FN(M, 1, 12) else if (mb == 8) FN(M, 1, 8) else FN(M, 1, 4) \
+            if (mb == 16) FN(M, 2, 16) else if (mb == 12) FN(M, 2, 12) else if (mb == 8) FN(M, 2, 8) else FN(M, 2, 4) \
         }                                                                                 \
     }
 
@@ -682,7 +706,7 @@ int step_ctas_per_sm(const Scal& S, const Launch& L)
 {
     int occ = 1;
 #define GBMD_OCC(M, NB, MB) { occ = occ_of<M, NB, MB>(); }
-    if (S.mode == MD_FP64) occ = occ_of<MD_FP64, 1, 4>();
+    if (S.mode == MD_FP64) occ = occ_of<MD_FP64, 2, 4>();
     else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_OCC)
     else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_OCC)
 #undef GBMD_OCC
@@ -697,7 +721,7 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
         if (props) k_step<M, true, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);  \
         else k_step<M, false, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);       \
     }
-    if (S.mode == MD_FP64) GBMD_STEP(MD_FP64, 1, 4)
+    if (S.mode == MD_FP64) GBMD_STEP(MD_FP64, 2, 4)
     else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
     else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)
 #undef GBMD_STEP

@@ -20,8 +20,8 @@ import time
 import torch
 
 CTAS = (4, 8, 12, 16)
-NBR_BATCH = (1, 2, 4)
-BUILD_BATCH = (1, 2, 4, 32)
+NBR_BATCH = (2, 4, 8)
+BUILD_BATCH = (2, 4, 32)
 
 
 def signature(system) -> str:

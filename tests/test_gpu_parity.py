@@ -160,7 +160,7 @@ def test_launch_shapes_do_not_change_results():
     ref, *_ = make("wca1372", "mixed")
     ref.integrate(64)
     xr, vr, _ = ref.state()
-    for ctas, nb, bb in ((4, 1, 1), (8, 4, 4), (16, 2, 2), (12, 1, 4), (8, 2, 32)):
+    for ctas, nb, bb in ((4, 2, 2), (8, 4, 4), (16, 8, 2), (12, 2, 4), (8, 8, 32)):
         s, *_ = make("wca1372", "mixed")
         s.set_tuning(ctas_per_sm=ctas, nbr_batch=nb, build_batch=bb)
         s.integrate(64)
