@@ -209,13 +209,10 @@ def run_gb300(args, rank, world, local_rank):
     issued = s.timing()
     props = s.props()
     rebuilds_timed = sum(p["rebuilds"] - r0 for p, r0 in zip(props, rb0))
-    # kernels that ran: the host-issued ones plus, inside captured graphs, the 10 kernels of
-    # every rebuild whose IF node opened (11 kernels; a batch runs one sequence for all replicas)
+    # kernels that ran: the library counts the host-issued ones and, inside captured graphs, the
+    # kernels of every rebuild sequence whose IF node opened (a device counter it reads back)
     graph_mode = s.tuning()["use_graph"] == 1
     launches = sum(p[2] for p in issued.values())
-    if graph_mode:
-        nrb = max(p["rebuilds"] - r0 for p, r0 in zip(props, rb0)) if s.nrep == 1 else rebuilds_timed
-        launches += 11 * int(nrb)
     mean_nbrs = float(np.average([p["mean_nbrs"] for p in props], weights=s.n_rep))
     if world > 1:
         ms, total_atoms, value = combine_ranks(ms, n, args.steps, device=dev)

@@ -198,6 +198,14 @@ typedef struct {
                                 candidates staged once in shared memory (for cells of tens of
                                 atoms) */
     int32_t use_graph;       /* 1: md_integrate replays captured CUDA graphs; 2: direct launches */
+    int32_t step_kernel;     /* fused step kernel (MD_MIXED, MD_FP32): 1 = each thread loads its
+                                atom's state and W column, the next tile prefetched into L2;
+                                2 = the tile's state and W rows copied into a two-stage
+                                shared-memory ring by cp.async.bulk, completing on mbarriers;
+                                3 = as 1, with each tile's neighbour positions first copied into
+                                shared memory by cp.async.bulk (one slot window per row of
+                                neighbour cells; compact when atoms are reordered at every
+                                rebuild, reorder_every = 0) */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);

@@ -167,6 +167,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     if (P.rule == MD_REBUILD_DISP) a.xref = c.take<float4>(ns);
     a.perm = c.take<int32_t>(ns);
     if (!f64) a.psort = c.take<float4>(ns);
+    if (!f64) a.tile_win = c.take<int2>(size_t(P.ntiles) * 9);
     if (!f32) for (int q = 0; q < 3; ++q) a.tmp_d[q] = c.take<double>(ns);
     for (int q = 0; q < 3; ++q) a.tmp_v[q] = c.take<double>(ns);
     for (int q = 0; q < 2; ++q) a.tmp_i[q] = c.take<int32_t>(ns);
@@ -214,6 +215,8 @@ struct md_system {
     Launch L;
     int cur = 0;
     int nsm = 0;
+    int smem_per_sm = 0;          // shared memory per SM and the per-CTA opt-in maximum, bytes
+    int smem_per_cta = 0;
     int64_t host_step = 0;
     bool binned_fresh = false;
     md_tuning tune;
@@ -373,6 +376,9 @@ int apply_tuning(md_system* s)
     s->L.build_block = TILE;
     s->L.nbr_batch = s->tune.nbr_batch;
     s->L.build_batch = s->tune.build_batch;
+    s->L.step_kernel = (s->S.mode == MD_FP64) ? 1 : s->tune.step_kernel;
+    bulk_shape(s->S, per_sm, s->smem_per_sm, s->smem_per_cta, &s->L.bulk_rows, &s->L.bulk_smem);
+    stage_shape(per_sm, s->smem_per_sm, &s->L.stage_cap, &s->L.stage_smem);
     s->L.ctas_req = per_sm;
     // a persistent grid larger than what can be resident would run as a trailing second wave
     s->L.grid_step = s->nsm * std::min(per_sm, step_ctas_per_sm(s->S, s->L));
@@ -542,10 +548,13 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     cudaError_t e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
     s->nsm = prop.multiProcessorCount;
+    s->smem_per_sm = int(prop.sharedMemPerMultiprocessor);
+    s->smem_per_cta = int(prop.sharedMemPerBlockOptin);
     s->tune.ctas_per_sm = 12;
     s->tune.nbr_batch = 4;
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
+    s->tune.step_kernel = 1;
     apply_tuning(s);
 
     auto bail = [&](int code) { delete s; return code; };
@@ -615,7 +624,7 @@ int md_integrate(md_system* s, int32_t nsteps)
     if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
     if (nsteps < 0) return fail(MD_ERR_INVALID_ARG, "nsteps < 0");
     if (s->binned_fresh) {      // a md_bin_cells without md_build_neighbours: finish the rebuild
-        Phase t(s, MD_PHASE_BUILD, 2);
+        Phase t(s, MD_PHASE_BUILD, 3);
         GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
         s->binned_fresh = false;
     }
@@ -665,7 +674,7 @@ int md_integrate(md_system* s, int32_t nsteps)
             GBMD_CUDA(launch_reorder(s->A, s->S, s->L, s->cur));
         }
         {
-            Phase t(s, MD_PHASE_BUILD, 2);
+            Phase t(s, MD_PHASE_BUILD, 3);
             GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
         }
         s->host_step += 1;
@@ -845,10 +854,12 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->build_batch && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
         return fail(MD_ERR_INVALID_ARG, "build_batch must be 2, 4 or 32");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
+    if (t->step_kernel < 0 || t->step_kernel > 3) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0, 1, 2 or 3");
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
     if (t->build_batch) s->tune.build_batch = t->build_batch;
     if (t->use_graph) s->tune.use_graph = t->use_graph;
+    if (t->step_kernel) s->tune.step_kernel = t->step_kernel;
     s->drop_graphs();          // launch shapes are baked into captured graphs
     return apply_tuning(s);
 }

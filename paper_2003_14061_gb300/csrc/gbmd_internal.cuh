@@ -96,6 +96,8 @@ struct Arrays {
     float4* xref;             // positions at the last rebuild (rule DISP)
     int32_t* perm;            // cell-ordered slots (the matrix H of Sec. 2.3, flattened)
     float4* psort;            // FP32 positions in cell order, slot in .w (MD_MIXED, MD_FP32)
+    int2* tile_win;           // [ntiles][9] slot window (lo, hi) of each tile's W entries per
+                              // (o_y, o_z) row, periodic-wrap entries excluded (MD_MIXED, MD_FP32)
     // reorder scratch, per slot
     double* tmp_d[3];
     double* tmp_v[3];
@@ -209,6 +211,93 @@ __device__ __forceinline__ long long warp_sum_ll(long long x)
 }
 
 // ------------------------------------------------------------------------------------------
+// bulk asynchronous copies global -> shared (cp.async.bulk, the TMA engine's linear mode)
+// completing on an mbarrier in shared memory
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// makes initialised mbarriers visible to the asynchronous proxy (the copy engine)
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// one arrival that also raises the transaction count the phase waits for by `bytes`
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of the given parity to complete, for one second at most; false if it
+// gave up (the caller latches ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+// `bytes` (a multiple of 16) from global src to shared dst, both 16-byte aligned; completes as
+// transactions on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// One stage of the step kernel's shared-memory ring: a tile's FP32 positions, its velocity
+// (and, MD_MIXED, FP64 position) streams, its neighbour counts and `rows` rows of W.  Every
+// offset is a multiple of 512 bytes.
+struct StageLayout {
+    uint32_t pos, xl, v, cnt, w, bytes;
+};
+
+__host__ __device__ inline StageLayout stage_layout(int mode, int rows)
+{
+    StageLayout L;
+    uint32_t o = 0;
+    L.pos = o;
+    o += TILE * 16u;
+    L.xl = o;
+    if (mode == MD_MIXED) o += 3u * TILE * 8u;
+    L.v = o;
+    o += 3u * TILE * ((mode == MD_MIXED) ? 8u : 4u);
+    L.cnt = o;
+    o += TILE * 4u;
+    L.w = o;
+    o += uint32_t(rows) * TILE * 4u;
+    L.bytes = o;
+    return L;
+}
+
+// ------------------------------------------------------------------------------------------
 // host-side launch wrappers (defined in the .cu files)
 // ------------------------------------------------------------------------------------------
 struct Launch {
@@ -217,9 +306,15 @@ struct Launch {
     int grid_step;            // persistent CTAs of the step kernel (capped at its occupancy)
     int step_block;
     int build_block;
-    int nbr_batch;            // W entries loaded together per thread in the pair loop (1, 2, 4)
+    int nbr_batch;            // W entries loaded together per thread in the pair loop (2, 4, 8)
     int ctas_req;             // requested resident CTAs/SM (register bound of the step kernel)
-    int build_batch;          // candidates loaded together per thread in the build (1, 2, 4)
+    int build_batch;          // candidates loaded together per thread in the build (2, 4; 32 = warp per cell)
+    int step_kernel;          // 1: per-thread loads with L2 prefetch; 2: bulk-copy shared-memory ring;
+                              // 3: as 1, with each tile's neighbour positions staged in shared memory
+    int bulk_rows;            // rows of W staged per tile by the ring (step_kernel 2)
+    int bulk_smem;            // dynamic shared memory of the ring kernel, bytes
+    int stage_cap;            // neighbour positions staged per tile (step_kernel 3)
+    int stage_smem;           // dynamic shared memory of the staged step kernel, bytes
     cudaGraphConditionalHandle cond;   // IF node of the rebuild (inside a captured graph)
     int use_cond;             // 1 while capturing md_integrate into a graph
     int in_graph;             // 1 while capturing an IF-node body (counts rebuild sequences)
@@ -234,8 +329,8 @@ cudaError_t launch_rebuild(const Arrays& A, const Scal& S, const Launch& L, int 
 cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
 cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);   // 7 kernels
 cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur);                    // 2 kernels
-cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur);                // 2 kernels
-constexpr int REBUILD_KERNELS = 11;       // kernels of one rebuild sequence (bin/order 7, reorder 2, build 2)
+cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur);                // 3 kernels
+constexpr int REBUILD_KERNELS = 12;       // kernels of one rebuild sequence (bin/order 7, reorder 2, build 3)
 
 // adjoint (kernels_adjoint.cu)
 cudaError_t launch_adj_reverse(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int q, double kappa,
@@ -247,6 +342,10 @@ cudaError_t launch_adj_final(const AdjView& V, const Launch& L, int ntiles);
 // step path (kernels_step.cu)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props);
 int step_ctas_per_sm(const Scal& S, const Launch& L);     // resident CTAs/SM of the chosen k_step
+// rows of W and dynamic shared memory of the ring kernel for ctas_per_sm resident CTAs/SM
+void bulk_shape(const Scal& S, int ctas_per_sm, int smem_per_sm, int smem_per_cta, int* rows, int* smem_bytes);
+// neighbour positions staged per tile and dynamic shared memory of step kernel 3
+void stage_shape(int ctas_per_sm, int smem_per_sm, int* cap, int* smem_bytes);
 cudaError_t launch_forces(const Arrays& A, const Scal& S, const Launch& L, int cur);
 cudaError_t launch_props(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_forces,
                          bool to_series);

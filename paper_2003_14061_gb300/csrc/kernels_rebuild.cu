@@ -919,6 +919,80 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
 }
 
 // ------------------------------------------------------------------------------------------
+// Slot windows of each rebuilt tile's neighbours, for the step kernel that stages neighbour
+// positions in shared memory: for every (o_y, o_z) row code, the smallest and largest slot among
+// the tile's W entries of that code whose neighbour cell is reached without a periodic wrap
+// (wrapped entries are gathered from global memory).  With atoms in cell order (reorder at every
+// rebuild) each window spans the tile's cells plus one halo cell at either end, in one row of
+// cells; otherwise windows can be wide, and the step kernel then stages what fits its budget.
+// One CTA per tile; empty rows get lo > hi.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) k_tile_windows(Arrays A, Scal S, int cur, int enabled)
+{
+    __shared__ int sh_lo[9], sh_hi[9];
+    if (!enabled || !A.g->any_rebuild || !A.tile_win) return;
+    const int nrb = A.g->n_rb_tiles;
+    for (int it = blockIdx.x; it < nrb; it += gridDim.x) {
+        const int t = A.rb_tiles[it];
+        const Rep& R = A.rep[A.tile_rep[t]];
+        if (threadIdx.x < 9) {
+            sh_lo[threadIdx.x] = INT32_MAX;
+            sh_hi[threadIdx.x] = -1;
+        }
+        __syncthreads();
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        if (slot - R.slot0 < R.n) {
+            int cx, cy, cz;
+            unpack_cell(__float_as_uint(A.pos32[cur][slot].w), cx, cy, cz);
+            // codes whose neighbour cell lies across the periodic boundary for this atom
+            const bool wxl = cx == 0, wxh = cx == R.nc[0] - 1, wyl = cy == 0, wyh = cy == R.nc[1] - 1;
+            const bool wzl = cz == 0, wzh = cz == R.nc[2] - 1;
+            int lo[9], hi[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                lo[q] = INT32_MAX;
+                hi[q] = -1;
+            }
+            const int mm = min(A.nbr_count[slot], S.cap);
+            constexpr int B = 4;                 // rows of W loaded together
+            for (int m0 = 0; m0 < mm; m0 += B) {
+              uint32_t eb[B];
+#pragma unroll
+              for (int u = 0; u < B; ++u) eb[u] = (m0 + u < mm) ? __ldcs(A.W + int64_t(m0 + u) * S.nslots + slot) : 0u;
+#pragma unroll
+              for (int u = 0; u < B; ++u) {
+                if (m0 + u >= mm) break;
+                const uint32_t e = eb[u];
+                const uint32_t ox = e & 3u, oy = (e >> 2) & 3u, oz = (e >> 4) & 3u;
+                const bool wrap = (ox == 0 && wxl) || (ox == 2 && wxh) || (oy == 0 && wyl) || (oy == 2 && wyh) ||
+                                  (oz == 0 && wzl) || (oz == 2 && wzh);
+                if (wrap) continue;
+                const int j = int(e >> IDX_SHIFT);
+                const int q = int(oy + 3 * oz);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    if (k == q) {
+                        lo[k] = min(lo[k], j);
+                        hi[k] = max(hi[k], j);
+                    }
+                }
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                if (hi[k] >= 0) {
+                    atomicMin(&sh_lo[k], lo[k]);
+                    atomicMax(&sh_hi[k], hi[k]);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 9) A.tile_win[int64_t(t) * 9 + threadIdx.x] = make_int2(sh_lo[threadIdx.x], sh_hi[threadIdx.x]);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // bookkeeping after a rebuild
 // ------------------------------------------------------------------------------------------
 __global__ void k_rebuild_finish(Arrays A, Scal S, int in_graph)
@@ -1015,6 +1089,7 @@ cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, i
     else if (L.build_batch >= 32) k_build_cw<<<std::max(1, L.grid), TILE, 0, L.stream>>>(A, S, cur);
     else if (L.build_batch >= 4) k_build_sorted<4><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else k_build_sorted<2><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    k_tile_windows<<<g, TILE, 0, L.stream>>>(A, S, cur, L.step_kernel == 3 ? 1 : 0);   // used by step kernel 3
     k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S, L.in_graph);
     return cudaGetLastError();
 }

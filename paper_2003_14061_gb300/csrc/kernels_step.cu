@@ -41,19 +41,18 @@ __device__ __forceinline__ float rcp_approx(float x)
 struct AccF { float fx, fy, fz, u, w; };
 struct AccD { double fx, fy, fz, u, w; };
 
-// One thread per atom over its column of W, NB entries at a time.  The row loads of batch b+1 are
-// issued together with the position gathers of batch b, so each thread keeps 2 NB loads in flight
-// and a batch waits for one memory latency, not two.  The arithmetic runs on packed FP32x2
-// operations (one instruction for two lanes, each lane rounded as the scalar operation): entries
-// 2k and 2k+1 of the column go to lanes x and y, and the two lanes' sums are added at the end, so
-// the summation order is the same for every NB.
-template <int NB>
-__device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const Rep& R,
-                                          const float4* __restrict__ pos, int64_t slot, float4 pi)
+// One thread per atom over its column of W, NB entries at a time; wr(m) returns the m-th entry
+// and pr(e) the FP32 cell-local position of the neighbour an entry names.
+// The entries of batch b+1 are read together with the position gathers of batch b, so each
+// thread keeps 2 NB loads in flight and a batch waits for one memory latency, not two.  The
+// arithmetic runs on packed FP32x2 operations (one instruction for two lanes, each lane rounded as
+// the scalar operation): entries 2k and 2k+1 of the column go to lanes x and y, and the two
+// lanes' sums are added at the end, so the summation order is the same for every NB and every
+// source of the entries.
+template <int NB, class WRead, class PRead>
+__device__ __forceinline__ AccF pair_loop_f32(const Scal& S, const Rep& R, float4 pi, int mm, WRead wr, PRead pr)
 {
     static_assert(NB % 2 == 0, "W entries are processed in pairs");
-    const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
-    const uint32_t* __restrict__ Wc = A.W + slot;
     const float2 wx = make_float2(R.wf[0], R.wf[0]);
     const float2 wy4 = make_float2(0.25f * R.wf[1], 0.25f * R.wf[1]);
     const float2 wz16 = make_float2(0.0625f * R.wf[2], 0.0625f * R.wf[2]);
@@ -62,15 +61,14 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, u = fx, w = fx;
     uint32_t e[NB];
 #pragma unroll
-    for (int k = 0; k < NB; ++k) e[k] = (k < mm) ? __ldcs(Wc + int64_t(k) * S.nslots) : 0u;
+    for (int k = 0; k < NB; ++k) e[k] = (k < mm) ? wr(k) : 0u;
     for (int m0 = 0; m0 < mm; m0 += NB) {
         float4 pj[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] >> IDX_SHIFT)) : pi;
+        for (int k = 0; k < NB; ++k) pj[k] = (m0 + k < mm) ? pr(e[k]) : pi;
         uint32_t en[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k)
-            en[k] = (m0 + NB + k < mm) ? __ldcs(Wc + int64_t(m0 + NB + k) * S.nslots) : 0u;
+        for (int k = 0; k < NB; ++k) en[k] = (m0 + NB + k < mm) ? wr(m0 + NB + k) : 0u;
 #pragma unroll
         for (int k = 0; k < NB; k += 2) {
             const uint32_t e0 = e[k], e1 = e[k + 1];
@@ -104,6 +102,71 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
     }
     // f_i = sum g (x_i - x_j) = -(sum g (x_j - x_i))
     return AccF{-(fx.x + fx.y), -(fy.x + fy.y), -(fz.x + fz.y), u.x + u.y, w.x + w.y};
+}
+
+// the pair loop with W read from global memory
+template <int NB>
+__device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const Rep& R,
+                                          const float4* __restrict__ pos, int64_t slot, float4 pi)
+{
+    const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
+    const uint32_t* __restrict__ Wc = A.W + slot;
+    const int64_t ns = S.nslots;
+    return pair_loop_f32<NB>(S, R, pi, mm, [=](int m) { return __ldcs(Wc + int64_t(m) * ns); },
+                             [=](uint32_t e) { return __ldg(pos + (e >> IDX_SHIFT)); });
+}
+
+// Leapfrog kick and drift of one atom (Sec. 4.3 item 1) from its force a: MD_MIXED advances the
+// FP64 state (v, x), MD_FP32 the FP32 velocity v32 and position pi; pn receives the FP32
+// cell-local position of step n+1.  Returns |x_{n+1} - x_n|^2 measured on the FP32 positions (the
+// refresh metric unless the rule is DISP).  With PROPS, part receives u_i, |v|^2, the virial and
+// the momentum at step n.
+template <int MODE, bool PROPS>
+__device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const float4& pi, const AccF& a,
+                                            double (&v)[3], double (&x)[3], float (&v32)[3], float (&pn)[3],
+                                            double (&part)[NPROP])
+{
+    const float f[3] = {a.fx, a.fy, a.fz};
+    double vn2 = 0.0;
+    if (MODE == MD_MIXED) {
+        const double kick = vhalf ? 2.0 * S.c : S.c;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const double fq = double(f[q]);
+            if (PROPS) {
+                const double vn = vhalf ? fma(S.c, fq, v[q]) : v[q];
+                vn2 = fma(vn, vn, vn2);
+                part[3 + q] = vn;
+            }
+            v[q] = fma(kick, fq, v[q]);
+            x[q] = fma(S.dt, v[q], x[q]);
+            pn[q] = __double2float_rn(x[q]);
+        }
+    } else {
+        const float kick = float(vhalf ? 2.0 * S.c : S.c);
+        const float cf = float(S.c), dtf = float(S.dt);
+        const float pc[3] = {pi.x, pi.y, pi.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (PROPS) {
+                const float vn = vhalf ? fmaf(cf, f[q], v32[q]) : v32[q];
+                vn2 = fma(double(vn), double(vn), vn2);
+                part[3 + q] = double(vn);
+            }
+            v32[q] = fmaf(kick, f[q], v32[q]);
+            pn[q] = fmaf(dtf, v32[q], pc[q]);
+        }
+    }
+    if (PROPS) {
+        part[0] = double(a.u);
+        part[1] = vn2;
+        part[2] = double(a.w);
+        part[NPROP - 1] = vn2;
+    }
+    // |x_{n+1} - x_n| = dt |v_{n+1/2}| from the FP32 copies of both positions (same cell frame);
+    // the per-step rounding margin is added in the finish
+    const float d0 = pn[0] - pi.x, d1 = pn[1] - pi.y, d2 = pn[2] - pi.z;
+    return fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p)
@@ -247,12 +310,31 @@ __device__ __forceinline__ void flush_replica(const Arrays& A, const Scal& S, in
 // ------------------------------------------------------------------------------------------
 // fused force + leapfrog step
 // ------------------------------------------------------------------------------------------
-template <int MODE, bool PROPS, int NB, int MINB>
+//
+// With STG (MD_MIXED, MD_FP32), the positions of each tile's neighbours are staged in shared
+// memory first: the tile's slot window per (o_y, o_z) row of W codes (k_tile_windows) is copied
+// by cp.async.bulk, as many windows as `stage_cap` positions hold, and the pair loop reads a
+// neighbour from shared memory unless its row was not staged or its cell is reached across the
+// periodic boundary (then from global memory).  The arithmetic is unchanged.
+template <int MODE, bool PROPS, int NB, int MINB, bool STG>
 __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
-                                                 int use_cond)
+                                                 int use_cond, int stage_cap)
 {
     __shared__ float sh_max[TILE / 32];
     __shared__ double sh_part[PROPS ? TILE / 32 : 1][NPROP];
+    extern __shared__ __align__(16) float4 s_nb[];       // STG: staged neighbour positions
+    __shared__ int4 sh_win[16];          // STG: per (o_y+1) + 4 (o_z+1): first slot, length, s_nb offset
+    __shared__ uint64_t sh_bar;
+    __shared__ int sh_staged;
+    uint32_t stg_parity = 0;
+    bool stg_timeout = false;
+    if (STG) {
+        if (threadIdx.x == 0) {
+            mbar_init(&sh_bar, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
     const int nxt = cur ^ 1;
     // Each CTA takes a contiguous run of tiles.  Software pipeline over them: while tile t is
     // computed, tile t+1's state and the rows of W below each atom's count are prefetched into
@@ -297,6 +379,39 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         const bool active = slot - R.slot0 < R.n;
         const int vhalf = A.rs[r].vhalf;
+        if (STG) {
+            // every thread is past its reads of the previous tile's staged positions
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                // windows in row order while they fit; a window that does not fit (or is empty)
+                // gets length 0 and its neighbours are read from global memory
+                const int2* wv = A.tile_win + int64_t(t) * 9;
+                int off = 0;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const int2 w = wv[q];
+                    const int len = w.y - w.x + 1;
+                    const bool fit = len > 0 && w.x >= 0 && int64_t(w.y) < S.nslots && off + len <= stage_cap;
+                    sh_win[(q % 3) + 4 * (q / 3)] = make_int4(w.x, fit ? len : 0, off, 0);
+                    if (fit) off += len;
+                }
+                if (off > 0) {
+                    mbar_arrive_expect_tx(&sh_bar, uint32_t(off) * 16u);
+                    const float4* pos = A.pos32[cur];
+#pragma unroll 1
+                    for (int q = 0; q < 9; ++q) {
+                        const int4 w = sh_win[(q % 3) + 4 * (q / 3)];
+                        if (w.y > 0) bulk_load(s_nb + w.z, pos + w.x, uint32_t(w.y) * 16u, &sh_bar);
+                    }
+                }
+                sh_staged = off > 0;
+            }
+            __syncthreads();
+            if (sh_staged) {
+                if (!stg_timeout && !mbar_wait_bounded(&sh_bar, stg_parity)) stg_timeout = true;
+                stg_parity ^= 1u;
+            }
+        }
         float metric = 0.0f;                     // |v|^2 (VMAX) or |x - x_ref|^2 (DISP)
         double part[NPROP];
 #pragma unroll
@@ -351,52 +466,49 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
                         for (int q = 0; q < 3; ++q) prefetch_l2(A.v32[q] + slot);
                     }
                 }
-                const AccF a = force_f32<NB>(A, S, R, pos, slot, pi);
-                const float f[3] = {a.fx, a.fy, a.fz};
-                float pn[3];
-                double vn2 = 0.0;
-                if (MODE == MD_MIXED) {
-                    const double kick = vhalf ? 2.0 * S.c : S.c;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        double v = __ldcs(A.v[q] + slot);
-                        const double fq = double(f[q]);
-                        if (PROPS) {
-                            const double vn = vhalf ? fma(S.c, fq, v) : v;
-                            vn2 = fma(vn, vn, vn2);
-                            part[3 + q] = vn;
-                        }
-                        v = fma(kick, fq, v);
-                        const double x = fma(S.dt, v, __ldcs(A.xl[q] + slot));
-                        __stcs(A.v[q] + slot, v);
-                        __stcs(A.xl[q] + slot, x);
-                        pn[q] = __double2float_rn(x);
-                    }
-                    // |x_{n+1} - x_n| = dt |v_{n+1/2}| from the FP32 copies of both positions
-                    // (same cell frame); the per-step rounding margin is added in the finish
-                    if (S.rule != MD_REBUILD_DISP) {
-                        const float d0 = pn[0] - pi.x, d1 = pn[1] - pi.y, d2 = pn[2] - pi.z;
-                        metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-                    }
+                AccF a;
+                if (STG) {
+                    // a neighbour inside its row's staged window is read from shared memory (the
+                    // window holds exactly those slots); any other from global memory
+                    const bool use_smem = !stg_timeout;
+                    const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
+                    const uint32_t* __restrict__ Wc = A.W + slot;
+                    const int64_t ns = S.nslots;
+                    a = pair_loop_f32<NB>(
+                        S, R, pi, mm, [=](int m) { return __ldcs(Wc + int64_t(m) * ns); },
+                        [=](uint32_t e) {
+                            const int j = int(e >> IDX_SHIFT);
+                            const int4 w = sh_win[(e >> 2) & 15u];
+                            const uint32_t d = uint32_t(j - w.x);
+                            const bool in = use_smem && d < uint32_t(w.y);
+                            const int si = in ? w.z + int(d) : 0;      // inside the staged range either way
+                            float4 r;
+                            if (in) r = s_nb[si];
+                            else r = __ldg(pos + j);
+                            return r;
+                        });
                 } else {
-                    const float kick = float(vhalf ? 2.0 * S.c : S.c);
-                    const float cf = float(S.c), dtf = float(S.dt);
-                    const float pc[3] = {pi.x, pi.y, pi.z};
+                    a = force_f32<NB>(A, S, R, pos, slot, pi);
+                }
+                double v[3], x[3];
+                float v32[3], pn[3];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        float v = A.v32[q][slot];
-                        if (PROPS) {
-                            const float vn = vhalf ? fmaf(cf, f[q], v) : v;
-                            vn2 = fma(double(vn), double(vn), vn2);
-                            part[3 + q] = double(vn);
-                        }
-                        v = fmaf(kick, f[q], v);
-                        A.v32[q][slot] = v;
-                        pn[q] = fmaf(dtf, v, pc[q]);
+                for (int q = 0; q < 3; ++q) {
+                    if (MODE == MD_MIXED) {
+                        v[q] = __ldcs(A.v[q] + slot);
+                        x[q] = __ldcs(A.xl[q] + slot);
+                    } else {
+                        v32[q] = A.v32[q][slot];
                     }
-                    if (S.rule != MD_REBUILD_DISP) {
-                        const float d0 = pn[0] - pi.x, d1 = pn[1] - pi.y, d2 = pn[2] - pi.z;
-                        metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                }
+                metric = kick_drift<MODE, PROPS>(S, vhalf, pi, a, v, x, v32, pn, part);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (MODE == MD_MIXED) {
+                        __stcs(A.v[q] + slot, v[q]);
+                        __stcs(A.xl[q] + slot, x[q]);
+                    } else {
+                        A.v32[q][slot] = v32[q];
                     }
                 }
                 A.pos32[nxt][slot] = make_float4(pn[0], pn[1], pn[2], pi.w);
@@ -404,12 +516,6 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
                     const float4 xr = A.xref[slot];
                     const float d0 = pn[0] - xr.x, d1 = pn[1] - xr.y, d2 = pn[2] - xr.z;
                     metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-                }
-                if (PROPS) {
-                    part[0] = double(a.u);
-                    part[1] = vn2;
-                    part[2] = double(a.w);
-                    part[NPROP - 1] = vn2;
                 }
             }
             if (!(metric <= 3.0e38f)) metric = __uint_as_float(0x7f800000u);   // +inf marks non-finite
@@ -422,6 +528,165 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
         }
     }
     if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+    if (STG && stg_timeout) atomicOr(&A.g->err, ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------------------------------------
+// fused force + leapfrog step through a shared-memory ring (MD_MIXED, MD_FP32)
+// ------------------------------------------------------------------------------------------
+// Each CTA takes a contiguous run of tiles and keeps two of them in a two-stage ring in shared
+// memory.  One thread issues a tile's cp.async.bulk copies (positions, velocity and position
+// streams, neighbour counts, and the rows of W below the tile's largest count, up to `rows`);
+// they complete on the stage's mbarrier.  The CTA waits on it, runs the same pair loop and
+// kick-drift as k_step with W and the state read from shared memory (only the neighbour
+// positions are gathered from global memory, through L1), and releases the stage, into which the
+// copies of the tile two ahead then go.  The HBM reads of the next tile are in flight while the
+// current one computes, without registers held for them.
+template <int MODE, bool PROPS, int NB>
+__global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur, int rows,
+                                                       cudaGraphConditionalHandle cond, int use_cond)
+{
+    extern __shared__ __align__(128) unsigned char ring[];
+    __shared__ uint64_t bar[2];
+    __shared__ float sh_max[TILE / 32];
+    __shared__ int sh_mm[2][TILE / 32];
+    __shared__ double sh_part[PROPS ? TILE / 32 : 1][NPROP];
+    const StageLayout SL = stage_layout(MODE, rows);
+    const int nxt = cur ^ 1;
+    const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per;
+    const int t_end = min(S.ntiles, t_begin + per);
+    if (t_begin >= t_end) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* __restrict__ pos = A.pos32[cur];
+
+    // the copies of tile t into stage st (thread 0); mmax = the tile's largest neighbour count
+    auto issue = [&](int t, int st, int mmax) {
+        unsigned char* sb = ring + size_t(st) * SL.bytes;
+        const int64_t s0 = int64_t(t) * TILE;
+        const int nr = min(min(mmax, S.cap), rows);
+        const uint32_t state = (MODE == MD_MIXED) ? 6u * TILE * 8u : 3u * TILE * 4u;
+        mbar_arrive_expect_tx(&bar[st], TILE * 16u + state + TILE * 4u + uint32_t(nr) * TILE * 4u);
+        bulk_load(sb + SL.pos, pos + s0, TILE * 16u, &bar[st]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (MODE == MD_MIXED) {
+                bulk_load(sb + SL.xl + q * TILE * 8, A.xl[q] + s0, TILE * 8u, &bar[st]);
+                bulk_load(sb + SL.v + q * TILE * 8, A.v[q] + s0, TILE * 8u, &bar[st]);
+            } else {
+                bulk_load(sb + SL.v + q * TILE * 4, A.v32[q] + s0, TILE * 4u, &bar[st]);
+            }
+        }
+        bulk_load(sb + SL.cnt, A.nbr_count + s0, TILE * 4u, &bar[st]);
+        for (int m = 0; m < nr; ++m)
+            bulk_load(sb + SL.w + uint32_t(m) * TILE * 4u, A.W + int64_t(m) * S.nslots + s0, TILE * 4u, &bar[st]);
+    };
+    auto block_mmax = [&](int st) {
+        int m = sh_mm[st][0];
+#pragma unroll
+        for (int k = 1; k < TILE / 32; ++k) m = max(m, sh_mm[st][k]);
+        return m;
+    };
+
+    // prologue: barriers, then the first two tiles
+    {
+        const int c0 = __ldcs(A.nbr_count + int64_t(t_begin) * TILE + threadIdx.x);
+        const int c1 = (t_begin + 1 < t_end) ? __ldcs(A.nbr_count + int64_t(t_begin + 1) * TILE + threadIdx.x) : 0;
+        const int m0 = warp_max_i(c0), m1 = warp_max_i(c1);
+        if (lane == 0) {
+            sh_mm[0][warp] = m0;
+            sh_mm[1][warp] = m1;
+        }
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            issue(t_begin, 0, block_mmax(0));
+            if (t_begin + 1 < t_end) issue(t_begin + 1, 1, block_mmax(1));
+        }
+    }
+    uint32_t parity = 0;                          // bit st: parity of stage st's next phase
+    bool timed_out = false;
+    int run_r = -1, run_tiles = 0;
+    float run_max = 0.0f;
+    for (int t = t_begin; t < t_end; ++t) {
+        const int st = (t - t_begin) & 1;
+        const int c2 = (t + 2 < t_end) ? __ldcs(A.nbr_count + int64_t(t + 2) * TILE + threadIdx.x) : 0;
+        {
+            const int r_t = A.tile_rep[t];
+            if (r_t != run_r) {
+                if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+                run_r = r_t;
+                run_tiles = 0;
+                run_max = 0.0f;
+            }
+        }
+        const int r = A.tile_rep[t];
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const bool active = slot - R.slot0 < R.n;
+        const int vhalf = A.rs[r].vhalf;
+        // after a wait that gave up the stage holds no valid data: this thread stops computing
+        // and waiting (its W entries would index garbage), and the error is latched at exit
+        if (!timed_out && !mbar_wait_bounded(&bar[st], (parity >> st) & 1u)) timed_out = true;
+        parity ^= 1u << st;
+        const unsigned char* sb = ring + size_t(st) * SL.bytes;
+        float metric = 0.0f;
+        double part[NPROP];
+#pragma unroll
+        for (int q = 0; q < NPROP; ++q) part[q] = 0.0;
+        if (active && !timed_out) {
+            const float4 pi = reinterpret_cast<const float4*>(sb + SL.pos)[threadIdx.x];
+            const int mm = min(reinterpret_cast<const int32_t*>(sb + SL.cnt)[threadIdx.x], S.cap);
+            const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + SL.w) + threadIdx.x;
+            const uint32_t* __restrict__ gw = A.W + slot;
+            const int64_t ns = S.nslots;
+            const AccF a = pair_loop_f32<NB>(
+                S, R, pi, mm, [=](int m) { return (m < rows) ? sw[m * TILE] : __ldcs(gw + int64_t(m) * ns); },
+                [=](uint32_t e) { return __ldg(pos + (e >> IDX_SHIFT)); });
+            double v[3], x[3];
+            float v32[3], pn[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (MODE == MD_MIXED) {
+                    v[q] = reinterpret_cast<const double*>(sb + SL.v)[q * TILE + threadIdx.x];
+                    x[q] = reinterpret_cast<const double*>(sb + SL.xl)[q * TILE + threadIdx.x];
+                } else {
+                    v32[q] = reinterpret_cast<const float*>(sb + SL.v)[q * TILE + threadIdx.x];
+                }
+            }
+            metric = kick_drift<MODE, PROPS>(S, vhalf, pi, a, v, x, v32, pn, part);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (MODE == MD_MIXED) {
+                    __stcs(A.v[q] + slot, v[q]);
+                    __stcs(A.xl[q] + slot, x[q]);
+                } else {
+                    __stcs(A.v32[q] + slot, v32[q]);
+                }
+            }
+            A.pos32[nxt][slot] = make_float4(pn[0], pn[1], pn[2], pi.w);
+            if (S.rule == MD_REBUILD_DISP) {
+                const float4 xr = A.xref[slot];
+                const float d0 = pn[0] - xr.x, d1 = pn[1] - xr.y, d2 = pn[2] - xr.z;
+                metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+            }
+            if (!(metric <= 3.0e38f)) metric = __uint_as_float(0x7f800000u);   // +inf marks non-finite
+        }
+        run_max = fmaxf(run_max, metric);
+        run_tiles += 1;
+        if (PROPS) tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
+        // release the stage (every thread is past its reads of it), then refill it with tile t+2
+        const int wm = warp_max_i(c2);
+        if (lane == 0) sh_mm[st][warp] = wm;
+        __syncthreads();
+        if (threadIdx.x == 0 && t + 2 < t_end && !timed_out) issue(t + 2, st, block_mmax(st));
+    }
+    if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+    if (timed_out) atomicOr(&A.g->err, ERR_TIMEOUT);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -674,12 +939,12 @@ static int tile_grid(const Scal& S, const Launch& L)
     return std::max(1, std::min(L.grid, S.ntiles));
 }
 
-template <int M, int NB, int MINB>
-static int occ_of()
+template <int M, int NB, int MINB, bool STG = false>
+static int occ_of(int dyn_smem = 0)
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<M, false, NB, MINB>, TILE, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<M, true, NB, MINB>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<M, false, NB, MINB, STG>, TILE, dyn_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<M, true, NB, MINB, STG>, TILE, dyn_smem);
     return std::max(1, std::min(a, b));
 }
 
@@ -702,12 +967,85 @@ static int minb_of(int ctas_per_sm)
         }                                                                                 \
     }
 
+// The dynamic shared-memory limit is a per-function setting: it is raised to the device's opt-in
+// maximum less the function's static shared memory, so systems with different ring sizes can
+// share the kernels.
+template <class K>
+static void raise_dyn_smem(K kernel)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes));
+}
+
+template <int M, int NB>
+static int occ_bulk(int smem)
+{
+    int a = 0, b = 0;
+    raise_dyn_smem(k_step_bulk<M, false, NB>);
+    raise_dyn_smem(k_step_bulk<M, true, NB>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_bulk<M, false, NB>, TILE, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_bulk<M, true, NB>, TILE, smem);
+    return std::max(1, std::min(a, b));
+}
+
+#define GBMD_DISPATCH_NB(M, FN)                                                           \
+    {                                                                                     \
+        const int nb = L.nbr_batch >= 8 ? 8 : L.nbr_batch >= 4 ? 4 : 2;                    \
+        if (nb == 8) FN(M, 8) else if (nb == 4) FN(M, 4) else FN(M, 2)                    \
+    }
+
+void bulk_shape(const Scal& S, int ctas_per_sm, int smem_per_sm, int smem_per_cta, int* rows, int* smem_bytes)
+{
+    // per CTA: the ring, its static shared memory (under 1 KB) and the 1 KB the runtime reserves
+    const int per_cta = std::min(smem_per_sm / std::max(1, ctas_per_sm) - 2048, smem_per_cta - 1024);
+    const int state = int(stage_layout(S.mode, 0).bytes);
+    int nr = (per_cta / 2 - state) / int(TILE * 4);
+    nr = std::max(1, std::min(nr, S.cap));
+    *rows = nr;
+    *smem_bytes = 2 * int(stage_layout(S.mode, nr).bytes);
+}
+
+template <int M, int NB, int MINB>
+static int occ_staged(int dyn_smem)
+{
+    raise_dyn_smem(k_step<M, false, NB, MINB, true>);
+    raise_dyn_smem(k_step<M, true, NB, MINB, true>);
+    return occ_of<M, NB, MINB, true>(dyn_smem);
+}
+
+void stage_shape(int ctas_per_sm, int smem_per_sm, int* cap, int* smem_bytes)
+{
+    // per CTA: the staged positions, the kernel's static shared memory and the runtime's 1 KB
+    const int per_cta = smem_per_sm / std::max(1, ctas_per_sm) - 2048;
+    const int c = std::max(256, std::min(per_cta / 16, 8192));
+    *cap = c;
+    *smem_bytes = c * 16;
+}
+
 int step_ctas_per_sm(const Scal& S, const Launch& L)
 {
     int occ = 1;
+    if (S.mode == MD_FP64) return occ_of<MD_FP64, 2, 4>();
+    if (L.step_kernel == 3) {
+#define GBMD_OCC(M, NB, MB) { occ = occ_staged<M, NB, MB>(L.stage_smem); }
+        if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_OCC)
+        else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_OCC)
+#undef GBMD_OCC
+        return occ;
+    }
+    if (L.step_kernel == 2) {
+#define GBMD_OCC(M, NB) { occ = occ_bulk<M, NB>(L.bulk_smem); }
+        if (S.mode == MD_MIXED) GBMD_DISPATCH_NB(MD_MIXED, GBMD_OCC)
+        else GBMD_DISPATCH_NB(MD_FP32, GBMD_OCC)
+#undef GBMD_OCC
+        return occ;
+    }
 #define GBMD_OCC(M, NB, MB) { occ = occ_of<M, NB, MB>(); }
-    if (S.mode == MD_FP64) occ = occ_of<MD_FP64, 2, 4>();
-    else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_OCC)
+    if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_OCC)
     else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_OCC)
 #undef GBMD_OCC
     return occ;
@@ -716,15 +1054,37 @@ int step_ctas_per_sm(const Scal& S, const Launch& L)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props)
 {
     const int g = std::max(1, std::min(L.grid_step, S.ntiles));
+    if (S.mode != MD_FP64 && L.step_kernel == 2) {
+#define GBMD_STEP_BULK(M, NB)                                                                               \
+    {                                                                                                       \
+        if (props) k_step_bulk<M, true, NB><<<g, TILE, L.bulk_smem, L.stream>>>(A, S, cur, L.bulk_rows, L.cond, L.use_cond); \
+        else k_step_bulk<M, false, NB><<<g, TILE, L.bulk_smem, L.stream>>>(A, S, cur, L.bulk_rows, L.cond, L.use_cond);     \
+    }
+        if (S.mode == MD_MIXED) GBMD_DISPATCH_NB(MD_MIXED, GBMD_STEP_BULK)
+        else GBMD_DISPATCH_NB(MD_FP32, GBMD_STEP_BULK)
+#undef GBMD_STEP_BULK
+    } else if (S.mode != MD_FP64 && L.step_kernel == 3) {
+#define GBMD_STEP_STG(M, NB, MB)                                                                       \
+    {                                                                                                  \
+        if (props)                                                                                     \
+            k_step<M, true, NB, MB, true><<<g, TILE, L.stage_smem, L.stream>>>(A, S, cur, L.cond, L.use_cond, L.stage_cap); \
+        else                                                                                           \
+            k_step<M, false, NB, MB, true><<<g, TILE, L.stage_smem, L.stream>>>(A, S, cur, L.cond, L.use_cond, L.stage_cap); \
+    }
+        if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP_STG)
+        else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP_STG)
+#undef GBMD_STEP_STG
+    } else {
 #define GBMD_STEP(M, NB, MB)                                                                           \
     {                                                                                                  \
-        if (props) k_step<M, true, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);  \
-        else k_step<M, false, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);       \
+        if (props) k_step<M, true, NB, MB, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);  \
+        else k_step<M, false, NB, MB, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);       \
     }
-    if (S.mode == MD_FP64) GBMD_STEP(MD_FP64, 2, 4)
-    else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
-    else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)
+        if (S.mode == MD_FP64) GBMD_STEP(MD_FP64, 2, 4)
+        else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
+        else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)
 #undef GBMD_STEP
+    }
     if (props) {
         k_props_slices<<<S.nrep * PROPS_SPLIT, 256, 0, L.stream>>>(A, S);
         k_props_finalize<<<S.nrep, 32, 0, L.stream>>>(A, S, 1, 1);

@@ -205,9 +205,11 @@ class MDSystem:
                    int(ckpt_every), ctypes.byref(loss), ctypes.byref(ge), ctypes.byref(gs), gptr)
         return loss.value, ge.value, gs.value, gv
 
-    def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0):
-        """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct."""
-        t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph))
+    def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0,
+                   step_kernel: int = 0):
+        """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct;
+        step_kernel: 1 = per-thread loads with L2 prefetch, 2 = bulk-copy shared-memory ring."""
+        t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph), int(step_kernel))
         self._call("md_set_tuning", ctypes.byref(t))
 
     def set_timing(self, enable: bool = True):

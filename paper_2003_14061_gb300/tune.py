@@ -7,9 +7,11 @@ system itself: every candidate advances the live system by a number of steps tim
 events on the library's stream.  All candidates perform the same arithmetic in the same order,
 so tuning never changes the trajectory.
 
-Search: coordinate descent over (ctas_per_sm, nbr_batch) for the step kernel, then build_batch
-for the neighbour build (timed over steps that include rebuilds).  Results are cached per GPU
-and workload signature in a JSON file.
+Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch) for the step -- the
+per-thread kernel at register-bound residencies, the shared-memory ring and the staged-neighbour
+kernel at the residencies their shared memory allows -- then build_batch for the neighbour build
+(timed over steps that include rebuilds).  Results are cached per GPU and workload signature in a
+JSON file.
 """
 from __future__ import annotations
 
@@ -19,7 +21,11 @@ import time
 
 import torch
 
-CTAS = (4, 8, 12, 16)
+from . import binding as B
+
+CTAS = (4, 8, 12, 16)          # per-thread step kernel (register-bound residency)
+CTAS_RING = (2, 3, 4, 6)       # shared-memory ring step kernel (shared-memory-bound residency)
+CTAS_STAGED = (4, 6, 8)        # staged-neighbour step kernel (register- and shared-memory-bound)
 NBR_BATCH = (2, 4, 8)
 BUILD_BATCH = (2, 4, 32)
 
@@ -69,16 +75,18 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
         return ms
 
     cur = system.tuning()
-    best = {"ctas_per_sm": cur["ctas_per_sm"], "nbr_batch": cur["nbr_batch"], "build_batch": cur["build_batch"]}
+    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel")}
     best_ms = trial(**best)
-    for ctas in CTAS:
-        for nb in NBR_BATCH:
-            cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb)
-            if json.dumps(cand, sort_keys=True) in trials:
-                continue
-            ms = trial(**cand)
-            if ms < best_ms:
-                best, best_ms = cand, ms
+    kernels = (1,) if system.params.precision == B.MD_FP64 else (1, 2, 3)
+    for sk in kernels:
+        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED}[sk]:
+            for nb in NBR_BATCH:
+                cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk)
+                if json.dumps(cand, sort_keys=True) in trials:
+                    continue
+                ms = trial(**cand)
+                if ms < best_ms:
+                    best, best_ms = cand, ms
     for bb in BUILD_BATCH:
         cand = dict(best, build_batch=bb)
         if json.dumps(cand, sort_keys=True) in trials:

@@ -160,12 +160,62 @@ def test_launch_shapes_do_not_change_results():
     ref, *_ = make("wca1372", "mixed")
     ref.integrate(64)
     xr, vr, _ = ref.state()
-    for ctas, nb, bb in ((4, 2, 2), (8, 4, 4), (16, 8, 2), (12, 2, 4), (8, 8, 32)):
+    for ctas, nb, bb, sk in ((4, 2, 2, 1), (8, 4, 4, 1), (16, 8, 2, 1), (12, 2, 4, 1), (8, 8, 32, 1),
+                             (4, 4, 4, 2), (6, 2, 2, 2), (2, 8, 32, 2), (8, 4, 2, 3), (4, 8, 4, 3),
+                             (12, 2, 32, 3)):
         s, *_ = make("wca1372", "mixed")
-        s.set_tuning(ctas_per_sm=ctas, nbr_batch=nb, build_batch=bb)
+        s.set_tuning(ctas_per_sm=ctas, nbr_batch=nb, build_batch=bb, step_kernel=sk)
         s.integrate(64)
         x, v, _ = s.state()
-        assert np.array_equal(x, xr) and np.array_equal(v, vr), (ctas, nb, bb)
+        assert np.array_equal(x, xr) and np.array_equal(v, vr), (ctas, nb, bb, sk)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("rule", ["vmax", "disp"])
+@pytest.mark.parametrize("ctas", [2, 8])
+@pytest.mark.parametrize("kernel,reorder", [(2, 100), (3, 0), (3, 100)])
+def test_shared_memory_kernels_match_per_thread_kernel(prec, rule, ctas, kernel, reorder):
+    # The shared-memory ring kernel (2) and the staged-neighbour kernel (3) run the same
+    # arithmetic as the per-thread kernel (1): states, rebuild counts and the per-step props rows
+    # agree bit for bit.  LJ (about 76 neighbours): at 8 CTAs/SM the ring holds fewer rows of W
+    # than the atoms use, so the rest are read from global memory; at 2 CTAs/SM most tiles fit.
+    # Kernel 3 with reorder at every rebuild stages compact windows; with reorder every 100 steps
+    # the windows widen and the rows that do not fit are gathered from global memory.
+    out = []
+    for sk in (1, kernel):
+        s, *_ = make("lj1372", prec, rebuild_rule=rule, props_every=1, reorder_every=reorder)
+        s.set_tuning(ctas_per_sm=ctas, nbr_batch=4, step_kernel=sk)
+        s.integrate(80)
+        x, v, _ = s.state()
+        out.append((x, v, s.props()[0]["rebuilds"], s.series()))
+        s.close()
+    (xa, va, ra, sa), (xb, vb, rb, sb) = out
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert ra == rb
+    assert np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_shared_memory_kernels_batched_replicas(kernel):
+    specs = inputs.replica_specs(9, 300, 4000, 0.6, 0.9, seed=11)
+    states = [(inputs.perturb(xr, br, 0.08, 60 + r), vr, br)
+              for r, (xr, vr, br) in enumerate(inputs.replica_states(specs, 1.0, seed=11))]
+    n_rep = [sp[0] for sp in specs]
+    boxes = np.stack([st[2] for st in states])
+    x = np.concatenate([st[0] for st in states])
+    v = np.concatenate([st[1] for st in states])
+    out = []
+    for sk in (1, kernel):
+        s = MDSystem(x, v, n_rep=n_rep, boxes=boxes, rc=WCA_RC, skin=0.4, precision="mixed", props_every=5,
+                     reorder_every=0)
+        s.set_tuning(step_kernel=sk)
+        s.integrate(60)
+        xs, vs, _ = s.state()
+        out.append((xs, vs, [p["rebuilds"] for p in s.props()], s.series()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    assert np.array_equal(out[0][3], out[1][3])
 
 
 def test_autotuner_picks_a_measured_shape(tmp_path):
