@@ -551,7 +551,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     s->smem_per_sm = int(prop.sharedMemPerMultiprocessor);
     s->smem_per_cta = int(prop.sharedMemPerBlockOptin);
     s->tune.ctas_per_sm = 12;
-    s->tune.nbr_batch = 4;
+    s->tune.nbr_batch = 2;
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
     s->tune.step_kernel = 1;

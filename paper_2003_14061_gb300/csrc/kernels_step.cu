@@ -353,15 +353,26 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
     for (int t = t_begin; t < t_end; ++t) {
         if (MODE != MD_FP64) {
             if (t + 1 < t_end) {
-                const int64_t s1 = int64_t(t + 1) * TILE + threadIdx.x;
-                prefetch_l2(A.pos32[cur] + s1);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (MODE == MD_MIXED) { prefetch_l2(A.xl[q] + s1); prefetch_l2(A.v[q] + s1); }
-                    else prefetch_l2(A.v32[q] + s1);
+                // one prefetch per 128-byte line, spread over the warp's lanes: the warp's 32
+                // slots span 4 lines of positions, 2 lines of each FP64 stream (1 of each FP32
+                // stream) and 1 line per row of W below the warp's largest count
+                const int lane = threadIdx.x & 31;
+                const int64_t w1 = int64_t(t + 1) * TILE + (threadIdx.x & ~31);
+                const int mw = min(__reduce_max_sync(0xffffffffu, unsigned(c_ahead)), unsigned(S.cap));
+                constexpr int NSTATE = (MODE == MD_MIXED) ? 12 : 3;      // lines of the state streams
+                for (int k = lane; k < 4 + NSTATE + mw; k += 32) {
+                    const void* p;
+                    if (k < 4) {
+                        p = A.pos32[cur] + w1 + 8 * k;
+                    } else if (k < 4 + NSTATE) {
+                        const int q = k - 4;
+                        if (MODE == MD_MIXED) p = ((q & 1) ? A.v[q >> 2] : A.xl[q >> 2]) + w1 + 16 * ((q >> 1) & 1);
+                        else p = A.v32[q] + w1;
+                    } else {
+                        p = A.W + int64_t(k - 4 - NSTATE) * S.nslots + w1;
+                    }
+                    prefetch_l2(p);
                 }
-                const int mm1 = min(c_ahead, S.cap);
-                for (int m = 0; m < mm1; ++m) prefetch_l2(A.W + int64_t(m) * S.nslots + s1);
             }
             c_ahead = (t + 2 < t_end) ? __ldcs(A.nbr_count + int64_t(t + 2) * TILE + threadIdx.x) : 0;
         }
