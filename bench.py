@@ -36,6 +36,7 @@ WORKLOADS = {
                      desc="512 WCA replicas, N ~ U{500..32000}, rho ~ U[0.6, 0.9]"),
 }
 METRIC = "particle-timesteps/s"
+RULE = "disp"          # rebuild when the largest displacement since the last rebuild exceeds skin/2
 UNIT = "particle-steps/s"
 DT = 0.005
 SEED = {"wca4m": 2, "lj16m": 3, "batch512": 4}
@@ -143,16 +144,18 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes_per_atom_step(mean_nbrs: float, precision: str = "mixed") -> float:
+def algorithmic_bytes_per_atom_step(mean_nbrs: float, precision: str = "mixed", rule: str = "vmax") -> float:
     """Bytes the fused step must move per atom (W counted at its mean row length).
 
     mixed: read pos32 16 + count 4 + W 4m + x 24 + v 24; write x 24 + v 24 + pos32 16.
+    The max-displacement rule also reads the position at the last rebuild (16).
     """
+    ref = 16.0 if rule == "disp" else 0.0
     if precision == "mixed":
-        return 132.0 + 4.0 * mean_nbrs
+        return 132.0 + ref + 4.0 * mean_nbrs
     if precision == "fp32":
-        return 16 + 4 + 12 + 16 + 12 + 4.0 * mean_nbrs
-    return 32 + 4 + 24 + 24 + 24 + 24 + 32 + 4.0 * mean_nbrs
+        return 16 + 4 + 12 + 16 + 12 + ref + 4.0 * mean_nbrs
+    return 32 + 4 + 24 + 24 + 24 + 24 + 32 + ref + 4.0 * mean_nbrs
 
 
 def cpu_oracle_rate(x, v, box, rc, steps, threads):
@@ -176,7 +179,7 @@ def run_gb300(args, rank, world, local_rank):
     x, v, geo = make_inputs(args.workload, rank, args.ncell)
     n = x.shape[0]
     s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
-                 rebuild_rule="vmax", **geo)
+                 rebuild_rule=RULE, **geo)
     if args.ctas_per_sm or args.nbr_batch or args.build_batch:
         s.set_tuning(ctas_per_sm=args.ctas_per_sm, nbr_batch=args.nbr_batch, build_batch=args.build_batch)
     tuned = None
@@ -230,7 +233,7 @@ def run_gb300(args, rank, world, local_rank):
     s.set_tuning(use_graph=2 if args.no_graph else 1)
     step_ms, step_calls, step_launches = phases["step"]
     peak, peak_kind = load_peaks()
-    bpa = algorithmic_bytes_per_atom_step(mean_nbrs)
+    bpa = algorithmic_bytes_per_atom_step(mean_nbrs, "mixed", RULE)
     per_launch_ms = step_ms / max(step_calls, 1)
     achieved = bpa * n / (per_launch_ms * 1e-3) / 1e9
 
@@ -239,7 +242,7 @@ def run_gb300(args, rank, world, local_rank):
     # memory; the state goes host-to-device at the start and device-to-host at the end
     e2e_steps = min(args.steps, args.e2e_steps)
     se = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
-                  rebuild_rule="vmax", props_every=1, **geo)
+                  rebuild_rule=RULE, props_every=1, **geo)
     se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch")})
     se.integrate(32)                                     # capture its graphs outside the timing
     xh = torch.from_numpy(x).pin_memory()
@@ -288,7 +291,7 @@ def run_gb300(args, rank, world, local_rank):
             "config": {"workload": w["desc"] if not args.ncell else f"{w['desc']} (resized: fcc {args.ncell}^3)",
                        "atoms_per_gpu": n, "precision": "FP32 pair forces, FP64 state",
                        "skin": w["skin"], "rc": w["rc"], "dt": DT, "reorder_every": 100,
-                       "rebuild_rule": "max-velocity bound > skin/2",
+                       "rebuild_rule": "max displacement since the last rebuild > skin/2",
                        "l2": "inputs larger than L2 (state %.2f GB)" % (s.workspace_bytes / 1e9),
                        "mean_neighbours": mean_nbrs,
                        "rebuilds_per_100_steps": 100.0 * rebuilds_timed / max(s.nrep, 1) / args.steps,

@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
                 const int64_t w1 = int64_t(t + 1) * TILE + (threadIdx.x & ~31);
                 const int mw = min(__reduce_max_sync(0xffffffffu, unsigned(c_ahead)), unsigned(S.cap));
                 constexpr int NSTATE = (MODE == MD_MIXED) ? 12 : 3;      // lines of the state streams
-                for (int k = lane; k < 4 + NSTATE + mw; k += 32) {
+                const int nref = (S.rule == MD_REBUILD_DISP) ? 4 : 0;     // positions at the last rebuild
+                for (int k = lane; k < 4 + NSTATE + nref + mw; k += 32) {
                     const void* p;
                     if (k < 4) {
                         p = A.pos32[cur] + w1 + 8 * k;
@@ -368,8 +369,10 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
                         const int q = k - 4;
                         if (MODE == MD_MIXED) p = ((q & 1) ? A.v[q >> 2] : A.xl[q >> 2]) + w1 + 16 * ((q >> 1) & 1);
                         else p = A.v32[q] + w1;
+                    } else if (k < 4 + NSTATE + nref) {
+                        p = A.xref + w1 + 8 * (k - 4 - NSTATE);
                     } else {
-                        p = A.W + int64_t(k - 4 - NSTATE) * S.nslots + w1;
+                        p = A.W + int64_t(k - 4 - NSTATE - nref) * S.nslots + w1;
                     }
                     prefetch_l2(p);
                 }
