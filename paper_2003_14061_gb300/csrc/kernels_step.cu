@@ -118,7 +118,8 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
 
 // Leapfrog kick and drift of one atom (Sec. 4.3 item 1) from its force a: MD_MIXED advances the
 // FP64 state (v, x), MD_FP32 the FP32 velocity v32 and position pi; pn receives the FP32
-// cell-local position of step n+1.  Returns |x_{n+1} - x_n|^2 measured on the FP32 positions (the
+// cell-local position of step n+1.  FP32<->FP64 conversions run on the integer pipe (bit for bit
+// the hardware ones).  Returns |x_{n+1} - x_n|^2 measured on the FP32 positions (the
 // refresh metric unless the rule is DISP).  With PROPS, part receives u_i, |v|^2, the virial and
 // the momentum at step n.
 template <int MODE, bool PROPS>
@@ -132,7 +133,7 @@ __device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const floa
         const double kick = vhalf ? 2.0 * S.c : S.c;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const double fq = double(f[q]);
+            const double fq = f32_to_f64(f[q]);
             if (PROPS) {
                 const double vn = vhalf ? fma(S.c, fq, v[q]) : v[q];
                 vn2 = fma(vn, vn, vn2);
@@ -140,7 +141,7 @@ __device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const floa
             }
             v[q] = fma(kick, fq, v[q]);
             x[q] = fma(S.dt, v[q], x[q]);
-            pn[q] = __double2float_rn(x[q]);
+            pn[q] = f64_to_f32(x[q]);
         }
     } else {
         const float kick = float(vhalf ? 2.0 * S.c : S.c);
@@ -150,17 +151,18 @@ __device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const floa
         for (int q = 0; q < 3; ++q) {
             if (PROPS) {
                 const float vn = vhalf ? fmaf(cf, f[q], v32[q]) : v32[q];
-                vn2 = fma(double(vn), double(vn), vn2);
-                part[3 + q] = double(vn);
+                const double vd = f32_to_f64(vn);
+                vn2 = fma(vd, vd, vn2);
+                part[3 + q] = vd;
             }
             v32[q] = fmaf(kick, f[q], v32[q]);
             pn[q] = fmaf(dtf, v32[q], pc[q]);
         }
     }
     if (PROPS) {
-        part[0] = double(a.u);
+        part[0] = f32_to_f64(a.u);
         part[1] = vn2;
-        part[2] = double(a.w);
+        part[2] = f32_to_f64(a.w);
         part[NPROP - 1] = vn2;
     }
     // |x_{n+1} - x_n| = dt |v_{n+1/2}| from the FP32 copies of both positions (same cell frame);
