@@ -240,6 +240,13 @@ struct md_system {
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graphs;
+    struct AdjGraph {                 // captured segments of md_adjoint (kind 0 forward, 1 recompute
+        const void* work;             // with snapshots, 2 reverse), for one adjoint workspace
+        int32_t nsteps, ckpt, kind, steps, buf0, flags;
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+    };
+    std::vector<AdjGraph> adj_graphs;
     int64_t host_series_rows = 0;     // series rows issued (props steps since creation/clear)
     cudaStream_t aux = nullptr;       // captures the IF-node bodies
     cudaStream_t gstream = nullptr;   // captures and replays the graphs (the caller's stream may be
@@ -253,6 +260,11 @@ struct md_system {
             cudaGraphDestroy(g.graph);
         }
         graphs.clear();
+        for (auto& g : adj_graphs) {
+            cudaGraphExecDestroy(g.exec);
+            cudaGraphDestroy(g.graph);
+        }
+        adj_graphs.clear();
     }
 
     cudaEvent_t take_event()
@@ -417,63 +429,72 @@ int load_state(md_system* s, const double* x, const double* v)
     return MD_OK;
 }
 
-// Capture `steps` steps starting from position buffer cur0 (bit j of props_mask: step j also
-// reduces the props into the time series).  Each step is the fused step kernel followed by an
-// IF node whose body is the rebuild sequence; the step kernel opens the IF node only when some
-// replica's refresh criterion fired, so steps without a rebuild launch nothing else.
-int capture_graph(md_system* s, int cur0, int steps, uint32_t props_mask, cudaGraphExec_t* out_exec)
+cudaError_t ensure_graph_streams(md_system* s)
 {
-    if (!s->aux) GBMD_CUDA(cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
-    if (!s->gstream) GBMD_CUDA(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
-    if (!s->ev_in) GBMD_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
-    if (!s->ev_out) GBMD_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+    cudaError_t e = cudaSuccess;
+    if (!s->aux) e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !s->gstream) e = cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !s->ev_in) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess && !s->ev_out) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+    return e;
+}
+
+// Inside a capture on stream st: the fused step kernel from position buffer cur (with S), then an
+// IF node whose body (captured on s->aux) is the rebuild sequence for the new buffer.  The step
+// kernel opens the node only when some replica's refresh criterion fired.
+cudaError_t capture_step_and_rebuild(md_system* s, const Scal& S, cudaStream_t st, int cur, bool props)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    cudaError_t err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
+    cudaGraphConditionalHandle h = 0;
+    if (err == cudaSuccess) err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    Launch L = s->L;
+    L.stream = st;
+    L.cond = h;
+    L.use_cond = 1;
+    if (err == cudaSuccess) err = launch_step(s->A, S, L, cur, props);
+    const int nxt = cur ^ 1;
+    if (err == cudaSuccess) err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (err == cudaSuccess) err = cudaGraphAddNode(&node, g, deps, ed, nd, &cp);
+    if (err == cudaSuccess) err = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (err == cudaSuccess)
+        err = cudaStreamBeginCaptureToGraph(s->aux, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        Launch Lb = s->L;
+        Lb.stream = s->aux;
+        Lb.use_cond = 0;
+        Lb.in_graph = 1;
+        cudaError_t e2 = launch_bin_order(s->A, S, Lb, nxt, false);
+        if (e2 == cudaSuccess) e2 = launch_reorder(s->A, S, Lb, nxt);
+        if (e2 == cudaSuccess) e2 = launch_build_only(s->A, S, Lb, nxt);
+        cudaGraph_t body = nullptr;
+        err = cudaStreamEndCapture(s->aux, &body);
+        if (err == cudaSuccess) err = e2;
+    }
+    return err;
+}
+
+// Captures what body(st) issues on the library's capture stream into an instantiated graph.
+template <class F>
+int capture_exec(md_system* s, F body, cudaGraph_t* g_out, cudaGraphExec_t* e_out)
+{
+    GBMD_CUDA(ensure_graph_streams(s));
     cudaStream_t st = s->gstream;
     GBMD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = cudaSuccess;
-    int cur = cur0;
-    for (int k = 0; k < steps && err == cudaSuccess; ++k) {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t g = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        const cudaGraphEdgeData* ed = nullptr;
-        size_t nd = 0;
-        err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
-        cudaGraphConditionalHandle h = 0;
-        if (err == cudaSuccess) err = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
-        Launch L = s->L;
-        L.stream = st;
-        L.cond = h;
-        L.use_cond = 1;
-        if (err == cudaSuccess) err = launch_step(s->A, s->S, L, cur, (props_mask >> k) & 1u);
-        cur ^= 1;
-        if (err == cudaSuccess) err = cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd);
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        if (err == cudaSuccess) err = cudaGraphAddNode(&node, g, deps, ed, nd, &cp);
-        if (err == cudaSuccess)
-            err = cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (err == cudaSuccess)
-            err = cudaStreamBeginCaptureToGraph(s->aux, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal);
-        if (err == cudaSuccess) {
-            Launch Lb = s->L;
-            Lb.stream = s->aux;
-            Lb.use_cond = 0;
-            Lb.in_graph = 1;
-            cudaError_t e2 = launch_bin_order(s->A, s->S, Lb, cur, false);
-            if (e2 == cudaSuccess) e2 = launch_reorder(s->A, s->S, Lb, cur);
-            if (e2 == cudaSuccess) e2 = launch_build_only(s->A, s->S, Lb, cur);
-            cudaGraph_t body = nullptr;
-            err = cudaStreamEndCapture(s->aux, &body);
-            if (err == cudaSuccess) err = e2;
-        }
-    }
+    cudaError_t err = body(st);
     cudaGraph_t graph = nullptr;
-    cudaError_t e_end = cudaStreamEndCapture(st, &graph);
+    const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
     if (err == cudaSuccess) err = e_end;
     if (err != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -486,6 +507,41 @@ int capture_graph(md_system* s, int cur0, int steps, uint32_t props_mask, cudaGr
         cudaGraphDestroy(graph);
         return fail(MD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(err));
     }
+    *g_out = graph;
+    *e_out = exec;
+    return MD_OK;
+}
+
+// Replays a graph on the capture stream, ordered after and before the caller's stream.
+int replay(md_system* s, cudaGraphExec_t exec)
+{
+    GBMD_CUDA(cudaEventRecord(s->ev_in, s->L.stream));
+    GBMD_CUDA(cudaStreamWaitEvent(s->gstream, s->ev_in, 0));
+    GBMD_CUDA(cudaGraphLaunch(exec, s->gstream));
+    GBMD_CUDA(cudaEventRecord(s->ev_out, s->gstream));
+    GBMD_CUDA(cudaStreamWaitEvent(s->L.stream, s->ev_out, 0));
+    return MD_OK;
+}
+
+// Capture `steps` steps starting from position buffer cur0 (bit j of props_mask: step j also
+// reduces the props into the time series).  Steps without a rebuild launch one kernel.
+int capture_graph(md_system* s, int cur0, int steps, uint32_t props_mask, cudaGraphExec_t* out_exec)
+{
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int rc = capture_exec(
+        s,
+        [&](cudaStream_t st) {
+            cudaError_t err = cudaSuccess;
+            int cur = cur0;
+            for (int k = 0; k < steps && err == cudaSuccess; ++k) {
+                err = capture_step_and_rebuild(s, s->S, st, cur, (props_mask >> k) & 1u);
+                cur ^= 1;
+            }
+            return err;
+        },
+        &graph, &exec);
+    if (rc) return rc;
     s->graphs.push_back({cur0, steps, props_mask, graph, exec});
     *out_exec = exec;
     return MD_OK;
@@ -645,12 +701,8 @@ int md_integrate(md_system* s, int32_t nsteps)
                 if (rc) return rc;
             }
             Phase t(s, MD_PHASE_STEP, G + 2 * __builtin_popcount(mask));
-            // replay on the library's stream, ordered after and before the caller's stream
-            GBMD_CUDA(cudaEventRecord(s->ev_in, s->L.stream));
-            GBMD_CUDA(cudaStreamWaitEvent(s->gstream, s->ev_in, 0));
-            GBMD_CUDA(cudaGraphLaunch(exec, s->gstream));
-            GBMD_CUDA(cudaEventRecord(s->ev_out, s->gstream));
-            GBMD_CUDA(cudaStreamWaitEvent(s->L.stream, s->ev_out, 0));
+            const int rc = replay(s, exec);
+            if (rc) return rc;
             k += G;
             s->host_step += G;
             s->host_series_rows += __builtin_popcount(mask);
@@ -895,6 +947,7 @@ size_t carve_adj(const md_system* s, const AdjPlan& P, char* base, AdjView* V)
         for (int a = 0; a < 3; ++a) {
             v.lx[b][a] = c.take<double>(ns);
             v.lv[b][a] = c.take<double>(ns);
+            v.mu[b][a] = c.take<double>(ns);
         }
     v.tile_acc = c.take<double>(size_t(s->plan.ntiles) * 4);
     v.ck_x = c.take<double>(n3 * (P.nseg + 1));
@@ -943,27 +996,69 @@ int adj_load(md_system* s, const Scal& S, const double* x, const double* v)
     return MD_OK;
 }
 
-int adj_step(md_system* s, const Scal& S, int& cur)
-{
-    Launch L = s->L;
-    L.use_cond = 0;
-    GBMD_CUDA(launch_step(s->A, S, L, cur, false));
-    cur ^= 1;
-    GBMD_CUDA(launch_bin_order(s->A, S, L, cur, false));
-    GBMD_CUDA(launch_reorder(s->A, S, L, cur));
-    GBMD_CUDA(launch_build_only(s->A, S, L, cur));
-    return MD_OK;
-}
-
-int adj_snapshot(md_system* s, const AdjView& V, int q, int cur)
+cudaError_t adj_snapshot(md_system* s, const AdjView& V, int q, int cur, cudaStream_t st)
 {
     const size_t ns = size_t(s->plan.nslots);
-    GBMD_CUDA(cudaMemcpyAsync(V.pos_snap + ns * q, s->A.pos32[cur], ns * sizeof(float4), cudaMemcpyDeviceToDevice,
-                              s->L.stream));
-    GBMD_CUDA(cudaMemcpyAsync(V.cnt_snap + ns * q, s->A.nbr_count, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice,
-                              s->L.stream));
-    GBMD_CUDA(cudaMemcpyAsync(V.W_snap + ns * size_t(s->plan.cap) * q, s->A.W, ns * size_t(s->plan.cap) * sizeof(uint32_t),
-                              cudaMemcpyDeviceToDevice, s->L.stream));
+    cudaError_t e = cudaMemcpyAsync(V.pos_snap + ns * q, s->A.pos32[cur], ns * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(V.cnt_snap + ns * q, s->A.nbr_count, ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(V.W_snap + ns * size_t(s->plan.cap) * q, s->A.W, ns * size_t(s->plan.cap) * sizeof(uint32_t),
+                            cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+// The graphs of md_adjoint's segments, captured once per (workspace, horizon, segment shape) and
+// replayed: kind 0 runs `steps` forward steps from buffer 0; kind 1 also snapshots the positions,
+// counts and W before the first and after every step; kind 2 walks the segment back (reverse
+// steps `steps`..1, plus step 0 in the first segment; flags bit 0: the segment ends at the
+// horizon, bit 1: it is the first).  Each step's rebuild sits behind an IF node as in md_integrate.
+int adj_graph(md_system* s, const Scal& Sa, const AdjView& V, const void* work, int nsteps, int ckpt, int kind, int steps,
+              int buf0, int flags, cudaGraphExec_t* out)
+{
+    for (auto& g : s->adj_graphs)
+        if (g.work == work && g.nsteps == nsteps && g.ckpt == ckpt && g.kind == kind && g.steps == steps &&
+            g.buf0 == buf0 && g.flags == flags) {
+            *out = g.exec;
+            return MD_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int rc = capture_exec(
+        s,
+        [&](cudaStream_t st) {
+            cudaError_t err = cudaSuccess;
+            if (kind == 0 || kind == 1) {
+                int cur = 0;
+                if (kind == 1) err = adj_snapshot(s, V, 0, cur, st);
+                for (int q = 1; q <= steps && err == cudaSuccess; ++q) {
+                    err = capture_step_and_rebuild(s, Sa, st, cur, false);
+                    cur ^= 1;
+                    if (err == cudaSuccess && kind == 1) err = adj_snapshot(s, V, q, cur, st);
+                }
+            } else {
+                Launch L = s->L;
+                L.stream = st;
+                int buf = buf0;
+                // kappa of reverse step q: 1 at the horizon and at n = 0, else 2
+                auto kappa_of = [&](int q) { return (((flags & 1) && q == steps) || q == 0) ? 1.0 : 2.0; };
+                err = launch_adj_permute(s->A, Sa, L, V, buf, true, kappa_of(steps));
+                for (int q = steps; q >= 1 && err == cudaSuccess; --q) {
+                    err = launch_adj_reverse(s->A, Sa, L, V, q, kappa_of(q), 1.0 / double(nsteps), buf, kappa_of(q - 1));
+                    buf ^= 1;
+                }
+                if (err == cudaSuccess && (flags & 2)) {
+                    err = launch_adj_reverse(s->A, Sa, L, V, 0, 1.0, 0.0, buf, 1.0);
+                    buf ^= 1;
+                }
+                if (err == cudaSuccess) err = launch_adj_permute(s->A, Sa, L, V, buf, false, 0.0);
+            }
+            return err;
+        },
+        &graph, &exec);
+    if (rc) return rc;
+    s->adj_graphs.push_back({work, nsteps, ckpt, kind, steps, buf0, flags, graph, exec});
+    *out = exec;
     return MD_OK;
 }
 
@@ -1006,13 +1101,12 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
     for (int k = 0; k < P.nseg; ++k) {
         rc = adj_load(s, Sa, V.ck_x + n3 * k, V.ck_v + n3 * k);
         if (rc) return rc;
-        int cur = 0;
         const int steps = std::min(P.K, P.S - k * P.K);
-        for (int q = 1; q <= steps; ++q) {
-            rc = adj_step(s, Sa, cur);
-            if (rc) return rc;
-        }
-        rc = adj_save(s, Sa, cur, V.ck_x + n3 * (k + 1), V.ck_v + n3 * (k + 1));
+        cudaGraphExec_t g = nullptr;
+        rc = adj_graph(s, Sa, V, d_work, nsteps, ckpt_every, 0, steps, 0, 0, &g);
+        if (!rc) rc = replay(s, g);
+        if (rc) return rc;
+        rc = adj_save(s, Sa, steps & 1, V.ck_x + n3 * (k + 1), V.ck_v + n3 * (k + 1));
         if (rc) return rc;
     }
     // terminal conditions and the |v_S|^2 part of the loss
@@ -1023,27 +1117,15 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
     for (int k = P.nseg - 1; k >= 0; --k) {
         rc = adj_load(s, Sa, V.ck_x + n3 * k, V.ck_v + n3 * k);
         if (rc) return rc;
-        int cur = 0;
-        rc = adj_snapshot(s, V, 0, cur);
-        if (rc) return rc;
         const int steps = std::min(P.K, P.S - k * P.K);
-        for (int q = 1; q <= steps; ++q) {
-            rc = adj_step(s, Sa, cur);
-            if (!rc) rc = adj_snapshot(s, V, q, cur);
-            if (rc) return rc;
-        }
-        GBMD_CUDA(launch_adj_permute(s->A, Sa, s->L, V, buf, true));
-        for (int q = steps; q >= 1; --q) {
-            const int n = k * P.K + q;
-            const double kappa = (n == P.S) ? 1.0 : 2.0;
-            GBMD_CUDA(launch_adj_reverse(s->A, Sa, s->L, V, q, kappa, 1.0 / double(P.S), buf));
-            buf ^= 1;
-        }
-        if (k == 0) {
-            GBMD_CUDA(launch_adj_reverse(s->A, Sa, s->L, V, 0, 1.0, 0.0, buf));
-            buf ^= 1;
-        }
-        GBMD_CUDA(launch_adj_permute(s->A, Sa, s->L, V, buf, false));
+        const int flags = (k == P.nseg - 1 ? 1 : 0) | (k == 0 ? 2 : 0);
+        cudaGraphExec_t gr = nullptr, gb = nullptr;
+        rc = adj_graph(s, Sa, V, d_work, nsteps, ckpt_every, 1, steps, 0, 0, &gr);
+        if (!rc) rc = replay(s, gr);
+        if (!rc) rc = adj_graph(s, Sa, V, d_work, nsteps, ckpt_every, 2, steps, buf, flags, &gb);
+        if (!rc) rc = replay(s, gb);
+        if (rc) return rc;
+        buf ^= (steps + (k == 0 ? 1 : 0)) & 1;
     }
     GBMD_CUDA(launch_adj_final(V, s->L, s->plan.ntiles));
     double out[8];

@@ -152,6 +152,7 @@ struct AdjView {
     uint32_t* W_snap;         // [K+1][cap][nslots] neighbour matrices
     double* lx[2][3];         // adjoint of positions, slot order, ping-pong
     double* lv[2][3];         // adjoint of velocities
+    double* mu[2][3];         // kappa (lv + dt lx) of the reverse step that reads buffer b
     double* tile_acc;         // [ntiles][4] running sums of the parameter terms and the loss
     double* ck_x;             // [nseg+1][n][3] FP64 checkpoints, id order
     double* ck_v;
@@ -393,8 +394,10 @@ constexpr int REBUILD_KERNELS = 12;       // kernels of one rebuild sequence (bi
 
 // adjoint (kernels_adjoint.cu)
 cudaError_t launch_adj_reverse(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int q, double kappa,
-                               double w_U, int in_buf);
-cudaError_t launch_adj_permute(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int buf, bool to_slot);
+                               double w_U, int in_buf, double kappa_next);
+// to_slot: kappa is that of the segment's first reverse step (its mu is written)
+cudaError_t launch_adj_permute(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int buf, bool to_slot,
+                               double kappa);
 cudaError_t launch_adj_init(const AdjView& V, const Launch& L, int64_t n, const double* vS);
 cudaError_t launch_adj_final(const AdjView& V, const Launch& L, int ntiles);
 

@@ -31,9 +31,15 @@ __device__ __forceinline__ float offx_a(uint32_t e) { return __uint_as_float(0x4
 __device__ __forceinline__ float offy4_a(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 12u)) - 8388612.0f; }
 __device__ __forceinline__ float offz16_a(uint32_t e) { return __uint_as_float(0x4B000000u | (e & 48u)) - 8388624.0f; }
 
-// one reverse step at the snapshot q of the current segment
+// One reverse step at the snapshot q of the current segment.  mu[in_buf] holds every atom's
+// mu = kappa lh of this step (written by the previous step or by the permute into slot order),
+// so a neighbour costs one FP64 3-vector gather; this step writes mu[out_buf] = kappa_next lh'
+// for the next one.  The neighbour loop runs NB entries at a time: their W rows, positions and mu
+// are loaded together.  FP32<->FP64 conversions run on the integer pipe (exact).
+constexpr int ADJ_NB = 4;
+
 __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView V, int q, double kappa, double w_U,
-                                                      int in_buf)
+                                                      int in_buf, double kappa_next)
 {
     __shared__ double sh[TILE / 32][4];
     const int out_buf = in_buf ^ 1;
@@ -42,6 +48,7 @@ __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView 
     const uint32_t* __restrict__ W = V.W_snap + int64_t(q) * S.cap * S.nslots;
     const double* lxi[3] = {V.lx[in_buf][0], V.lx[in_buf][1], V.lx[in_buf][2]};
     const double* lvi[3] = {V.lv[in_buf][0], V.lv[in_buf][1], V.lv[in_buf][2]};
+    const double* mu[3] = {V.mu[in_buf][0], V.mu[in_buf][1], V.mu[in_buf][2]};
     for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
         const Rep& R = A.rep[A.tile_rep[t]];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
@@ -52,54 +59,70 @@ __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView 
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 lh[a] = fma(S.dt, lxi[a][slot], lvi[a][slot]);
-                mui[a] = kappa * lh[a];
+                mui[a] = mu[a][slot];                                      // = kappa lh
             }
             double jm[3] = {0.0, 0.0, 0.0};
             float f[3] = {0.f, 0.f, 0.f}, fs[3] = {0.f, 0.f, 0.f};
             float u = 0.f, us = 0.f;
             const int mm = min(cnt[slot], S.cap);
             const float wx = R.wf[0], wy4 = 0.25f * R.wf[1], wz16 = 0.0625f * R.wf[2];
-            for (int m = 0; m < mm; ++m) {
-                const uint32_t e = W[int64_t(m) * S.nslots + slot];
-                const int64_t j = e >> IDX_SHIFT;
-                const float4 pj = pos[j];
-                const float dx = fmaf(offx_a(e), wx, pj.x - pi.x);     // d = x_j - x_i
-                const float dy = fmaf(offy4_a(e), wy4, pj.y - pi.y);
-                const float dz = fmaf(offz16_a(e), wz16, pj.z - pi.z);
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (r2 < S.rc2f) {
-                    const float ri2 = 1.0f / r2;
-                    const float sr2 = S.sig2f * ri2;
-                    const float sr6 = sr2 * sr2 * sr2;
-                    const float g = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;
-                    const float gp = S.eps48f * sr6 * (2.0f - 7.0f * sr6) * ri2 * ri2;
-                    const float gsg = S.adj_eps144_over_sig * sr6 * (4.0f * sr6 - 1.0f) * ri2;
-                    f[0] = fmaf(-g, dx, f[0]); f[1] = fmaf(-g, dy, f[1]); f[2] = fmaf(-g, dz, f[2]);
-                    fs[0] = fmaf(-gsg, dx, fs[0]); fs[1] = fmaf(-gsg, dy, fs[1]); fs[2] = fmaf(-gsg, dz, fs[2]);
-                    u += fmaf(S.eps4f * sr6, sr6 - 1.0f, -S.ucf);
-                    us += fmaf(S.adj_eps24_over_sig * sr6, 2.0f * sr6 - 1.0f, -S.adj_ducf);
-                    // mu_j on the fly from the neighbour's adjoint state (FP64), difference in FP64
-                    float dm[3];
+            for (int m0 = 0; m0 < mm; m0 += ADJ_NB) {
+                uint32_t e[ADJ_NB];
+                float4 pj[ADJ_NB];
+                double mj[ADJ_NB][3];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        dm[a] = float(mui[a] - kappa * fma(S.dt, lxi[a][j], lvi[a][j]));
-                    const float proj = 2.0f * gp * fmaf(dz, dm[2], fmaf(dy, dm[1], dx * dm[0]));
-                    jm[0] += double(fmaf(g, dm[0], proj * dx));
-                    jm[1] += double(fmaf(g, dm[1], proj * dy));
-                    jm[2] += double(fmaf(g, dm[2], proj * dz));
+                for (int k = 0; k < ADJ_NB; ++k) e[k] = (m0 + k < mm) ? W[int64_t(m0 + k) * S.nslots + slot] : 0u;
+#pragma unroll
+                for (int k = 0; k < ADJ_NB; ++k) {
+                    const bool ok = m0 + k < mm;
+                    const int64_t j = ok ? int64_t(e[k] >> IDX_SHIFT) : slot;
+                    pj[k] = pos[j];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) mj[k][a] = mu[a][j];
+                }
+#pragma unroll
+                for (int k = 0; k < ADJ_NB; ++k) {
+                    const uint32_t ek = e[k];
+                    const float dx = fmaf(offx_a(ek), wx, pj[k].x - pi.x);      // d = x_j - x_i
+                    const float dy = fmaf(offy4_a(ek), wy4, pj[k].y - pi.y);
+                    const float dz = fmaf(offz16_a(ek), wz16, pj[k].z - pi.z);
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    if (m0 + k < mm && r2 < S.rc2f) {
+                        const float ri2 = 1.0f / r2;
+                        const float sr2 = S.sig2f * ri2;
+                        const float sr6 = sr2 * sr2 * sr2;
+                        const float g = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;
+                        const float gp = S.eps48f * sr6 * (2.0f - 7.0f * sr6) * ri2 * ri2;
+                        const float gsg = S.adj_eps144_over_sig * sr6 * (4.0f * sr6 - 1.0f) * ri2;
+                        f[0] = fmaf(-g, dx, f[0]); f[1] = fmaf(-g, dy, f[1]); f[2] = fmaf(-g, dz, f[2]);
+                        fs[0] = fmaf(-gsg, dx, fs[0]); fs[1] = fmaf(-gsg, dy, fs[1]); fs[2] = fmaf(-gsg, dz, fs[2]);
+                        u += fmaf(S.eps4f * sr6, sr6 - 1.0f, -S.ucf);
+                        us += fmaf(S.adj_eps24_over_sig * sr6, 2.0f * sr6 - 1.0f, -S.adj_ducf);
+                        // mu_i - mu_j in FP64, then FP32 for the pair arithmetic
+                        float dm[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) dm[a] = f64_to_f32(mui[a] - mj[k][a]);
+                        const float proj = 2.0f * gp * fmaf(dz, dm[2], fmaf(dy, dm[1], dx * dm[0]));
+                        jm[0] += f32_to_f64(fmaf(g, dm[0], proj * dx));
+                        jm[1] += f32_to_f64(fmaf(g, dm[1], proj * dy));
+                        jm[2] += f32_to_f64(fmaf(g, dm[2], proj * dz));
+                    }
                 }
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                V.lx[out_buf][a][slot] = fma(S.c, jm[a], lxi[a][slot]) - w_U * double(f[a]);
+                const double fa = f32_to_f64(f[a]);
+                const double lxo = fma(S.c, jm[a], lxi[a][slot]) - w_U * fa;
+                V.lx[out_buf][a][slot] = lxo;
                 V.lv[out_buf][a][slot] = lh[a];
-                part[0] += double(f[a]) * mui[a];
-                part[1] += double(fs[a]) * mui[a];
+                V.mu[out_buf][a][slot] = kappa_next * fma(S.dt, lxo, lh[a]);
+                part[0] += fa * mui[a];
+                part[1] += f32_to_f64(fs[a]) * mui[a];
             }
             part[0] *= S.c;
             part[1] *= S.c;
-            part[2] = 0.5 * w_U * double(u);
-            part[3] = 0.5 * w_U * double(us);
+            part[2] = 0.5 * w_U * f32_to_f64(u);
+            part[3] = 0.5 * w_U * f32_to_f64(us);
         }
         // tile sums (4 FP64 values), added to this tile's running accumulators
 #pragma unroll
@@ -119,7 +142,8 @@ __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView 
 }
 
 // adjoint vectors between id order (kept across segments) and this segment's slot order
-__global__ void __launch_bounds__(TILE) k_adj_to_slot(Arrays A, Scal S, AdjView V, int buf)
+// (to slot order, also mu = kappa (lv + dt lx) for the segment's first reverse step)
+__global__ void __launch_bounds__(TILE) k_adj_to_slot(Arrays A, Scal S, AdjView V, int buf, double kappa)
 {
     for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
         const Rep& R = A.rep[A.tile_rep[t]];
@@ -128,8 +152,10 @@ __global__ void __launch_bounds__(TILE) k_adj_to_slot(Arrays A, Scal S, AdjView 
         const int64_t id = A.id[slot];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            V.lx[buf][a][slot] = V.lam_x[id * 3 + a];
-            V.lv[buf][a][slot] = V.lam_v[id * 3 + a];
+            const double lx = V.lam_x[id * 3 + a], lv = V.lam_v[id * 3 + a];
+            V.lx[buf][a][slot] = lx;
+            V.lv[buf][a][slot] = lv;
+            V.mu[buf][a][slot] = kappa * fma(S.dt, lx, lv);
         }
     }
 }
@@ -190,15 +216,16 @@ __global__ void __launch_bounds__(256) k_adj_final(AdjView V, int ntiles, int nv
 static int tile_grid(const Scal& S, const Launch& L) { return std::max(1, std::min(L.grid, S.ntiles)); }
 
 cudaError_t launch_adj_reverse(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int q, double kappa,
-                               double w_U, int in_buf)
+                               double w_U, int in_buf, double kappa_next)
 {
-    k_adj_reverse<<<tile_grid(S, L), TILE, 0, L.stream>>>(A, S, V, q, kappa, w_U, in_buf);
+    k_adj_reverse<<<tile_grid(S, L), TILE, 0, L.stream>>>(A, S, V, q, kappa, w_U, in_buf, kappa_next);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_permute(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int buf, bool to_slot)
+cudaError_t launch_adj_permute(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int buf, bool to_slot,
+                               double kappa)
 {
-    if (to_slot) k_adj_to_slot<<<tile_grid(S, L), TILE, 0, L.stream>>>(A, S, V, buf);
+    if (to_slot) k_adj_to_slot<<<tile_grid(S, L), TILE, 0, L.stream>>>(A, S, V, buf, kappa);
     else k_adj_to_id<<<tile_grid(S, L), TILE, 0, L.stream>>>(A, S, V, buf);
     return cudaGetLastError();
 }
