@@ -219,7 +219,9 @@ int md_get_tuning(const md_system* s, md_tuning* t);
  * pass recomputes one segment at a time from its checkpoint (checkpoint-and-recompute) and walks
  * it backwards with one force-Jacobian-vector-product kernel per step (FP32 pair arithmetic, FP64
  * accumulation).  sigma moves the cutoff with it when r_c = 2^(1/6) sigma (WCA); otherwise r_c is
- * held fixed.
+ * held fixed.  The segments run from CUDA graphs captured on first use and cached per (d_work,
+ * nsteps, ckpt_every, segment shape); md_set_tuning and md_destroy release them, and a call
+ * with another workspace or horizon captures its own.
  *   d_work     : device scratch of md_adjoint_workspace_bytes(s, nsteps, ckpt_every) bytes,
  *                256-byte aligned, owned by the caller (snapshots of one segment, checkpoints,
  *                adjoint vectors).

@@ -1022,6 +1022,16 @@ int adj_graph(md_system* s, const Scal& Sa, const AdjView& V, const void* work, 
             *out = g.exec;
             return MD_OK;
         }
+    // a bounded cache: callers that vary workspaces or horizons start it over
+    constexpr size_t ADJ_GRAPH_CACHE = 32;
+    if (s->adj_graphs.size() >= ADJ_GRAPH_CACHE) {
+        GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+        for (auto& g : s->adj_graphs) {
+            cudaGraphExecDestroy(g.exec);
+            cudaGraphDestroy(g.graph);
+        }
+        s->adj_graphs.clear();
+    }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const int rc = capture_exec(

@@ -60,6 +60,22 @@ def test_checkpoint_interval_does_not_change_gradients():
         assert rel_l2(r[3], res[0][3]) <= 1e-5
 
 
+def test_adjoint_graphs_follow_tuning_and_horizon():
+    # segments replay cached graphs; a new launch shape or horizon captures new ones, and the
+    # results do not depend on which graphs ran
+    x, v, box = small_case(11)
+    s = MDSystem(x, v, box, rc=WCA_RC, skin=0.4)
+    a = s.adjoint(30, 7)
+    s.set_tuning(ctas_per_sm=4, nbr_batch=8, build_batch=32)
+    b = s.adjoint(30, 7)
+    c = s.adjoint(30, 10)
+    s.set_tuning(ctas_per_sm=12, nbr_batch=2, build_batch=2)
+    d = s.adjoint(30, 7)
+    assert a[0] == b[0] == d[0] and a[1] == b[1] == d[1] and a[2] == b[2] == d[2]
+    assert np.array_equal(a[3], b[3]) and np.array_equal(a[3], d[3])
+    assert rel(c[0], a[0]) <= 1e-7 and rel(c[1], a[1]) <= 1e-5 and rel(c[2], a[2]) <= 1e-5
+
+
 def test_adjoint_is_deterministic():
     x, v, box = small_case(5)
     s = MDSystem(x, v, box, rc=WCA_RC, skin=0.4)
