@@ -54,15 +54,26 @@ def combine_ranks(ms: float, atoms: int, steps: int, device=None):
     return ms_max, total, total * steps / (ms_max * 1e-3)
 
 
-def traffic_per_atom(kernel: str):
-    """DRAM bytes per atom of a kernel from its committed ncu capture, if the source is unchanged."""
+def code_hash(path: str) -> str:
+    """sha256 (16 hex digits) of a C/CUDA source with comments and whitespace removed, so that
+    only code changes invalidate a capture taken on it."""
     import hashlib
+    import re
+    with open(path) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
+def traffic_per_atom(kernel: str):
+    """DRAM bytes per atom of a kernel from its committed ncu capture, if its code is unchanged."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)[kernel]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
-        return float(rec["dram_bytes_per_atom"]) if sha == rec["source_sha256_16"] else None
+        sha = code_hash(os.path.join(ROOT, rec["source"]))
+        return float(rec["dram_bytes_per_atom"]) if sha == rec["code_sha256_16"] else None
     except (OSError, KeyError, ValueError):
         return None
 

@@ -10,6 +10,11 @@
 //              Sec. 2.3, an atomic counter after a memory fence) updates the refresh criterion
 //              and raises the rebuild flag.  With PROPS, the tile also writes FP64 partial sums
 //              of U, K, virial and momentum (F2).
+//   k_step<..., STG = true>  the same with each tile's neighbour positions staged in shared
+//              memory by cp.async.bulk first (step kernel 3).
+//   k_step_bulk  the same arithmetic with the tile's state and W rows in a two-stage shared-memory
+//              ring filled by cp.async.bulk (step kernel 2).  The three forms share the pair loop
+//              and the kick-drift, so they give bit-identical trajectories.
 //   k_forces   F1 alone: f_i, u_i and the per-atom virial at the current positions.
 //   k_props_*  F2 and the other measured quantities: per-tile FP64 partials, then one CTA per
 //              replica sums them in a fixed order (deterministic).
@@ -221,7 +226,8 @@ __device__ __forceinline__ float tile_max(float v, float* sh)
 // Per-tile FP64 sums of the 7 additive quantities and the FP32 maximum of |v|^2.  The 8 doubles
 // of each lane are reduced across the warp by reduce-scatter (each exchange halves the number of
 // quantities a lane carries, 4 + 2 + 1 adds, then 2 more over the last 4 lanes): 9 FP64 adds per
-// lane instead of 35 for a butterfly per quantity (FP64 runs at 1/72 of the FP32 rate on GB300).
+// lane instead of 35 for a butterfly per quantity (FP64 runs at 1/64-1/72 of the FP32 rate on
+// GB300).
 __device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[NPROP], double* out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -316,8 +322,8 @@ __device__ __forceinline__ void flush_replica(const Arrays& A, const Scal& S, in
 // With STG (MD_MIXED, MD_FP32), the positions of each tile's neighbours are staged in shared
 // memory first: the tile's slot window per (o_y, o_z) row of W codes (k_tile_windows) is copied
 // by cp.async.bulk, as many windows as `stage_cap` positions hold, and the pair loop reads a
-// neighbour from shared memory unless its row was not staged or its cell is reached across the
-// periodic boundary (then from global memory).  The arithmetic is unchanged.
+// neighbour from shared memory when its slot lies in its row's staged window (which then holds
+// exactly that slot's position), else from global memory.  The arithmetic is unchanged.
 template <int MODE, bool PROPS, int NB, int MINB, bool STG>
 __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                  int use_cond, int stage_cap)

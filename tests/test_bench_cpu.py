@@ -68,3 +68,15 @@ def test_reference_arm_other_ranks_do_nothing():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "3",
                           "--warmup", "3"], capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_code_hash_ignores_comments_only(tmp_path):
+    import bench
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("// header\n__global__ void k(int* p) { p[0] = 1; /* note */ }\n")
+    b.write_text("// another header\n\n__global__ void k(int* p)\n{\n    p[0] = 1;  // same code\n}\n")
+    c.write_text("__global__ void k(int* p) { p[0] = 2; }\n")
+    assert bench.code_hash(str(a)) == bench.code_hash(str(b))
+    assert bench.code_hash(str(a)) != bench.code_hash(str(c))
