@@ -9,10 +9,15 @@
 //   k_scatter      N4: H flattened: perm[cstart[c] + l_i] = i.
 //   k_sort_cells   the atomic layer order is indeterminate (Sec. 2.3 notes the resulting
 //                  irreproducibility); sorting each cell's slots makes the order, and every
-//                  result after it, deterministic.
+//                  result after it, deterministic.  It also writes psort, the FP32 positions in
+//                  that order with each slot in .w, which the FP32 builds read.
 //   k_reorder_*    Sec. 4.1 item 1: permute the atoms into cell order (gather through scratch).
-//   k_build        N5: W from the 27 neighbouring cells; W stored row-major for coalescing
-//                  (Sec. 4.1 item 6).
+//   k_build_sorted N5 in FP32: W from the 27 neighbouring cells, one thread per atom, each row of
+//                  3 cells read as a contiguous run of psort; W stored row-major for coalescing
+//                  (Sec. 4.1 item 6).  k_build_cw: the same W with one warp per cell (cells of
+//                  tens of atoms).  k_build<double>: MD_FP64 through perm.
+//   k_tile_windows the slot window of each tile's W entries per row of neighbour cells, read by
+//                  the step kernel that stages neighbour positions (step kernel 3 only).
 // Only replicas whose rebuild flag is set do work; kernels return at once when none is set, so
 // the whole sequence can sit in every step of md_integrate.
 #include <algorithm>
