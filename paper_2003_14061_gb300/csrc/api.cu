@@ -252,6 +252,8 @@ struct md_system {
     cudaStream_t gstream = nullptr;   // captures and replays the graphs (the caller's stream may be
                                       // the legacy default stream, which cannot be captured)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t rstream = nullptr;   // md_adjoint's reverse walks, overlapping the recomputes
+    cudaEvent_t ev_rc[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
 
     void drop_graphs()
     {
@@ -287,6 +289,11 @@ struct md_system {
         if (gstream) cudaStreamDestroy(gstream);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        if (rstream) cudaStreamDestroy(rstream);
+        for (int k = 0; k < 2; ++k) {
+            if (ev_rc[k]) cudaEventDestroy(ev_rc[k]);
+            if (ev_rev[k]) cudaEventDestroy(ev_rev[k]);
+        }
     }
 };
 
@@ -436,6 +443,17 @@ cudaError_t ensure_graph_streams(md_system* s)
     if (e == cudaSuccess && !s->gstream) e = cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !s->ev_in) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess && !s->ev_out) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+    return e;
+}
+
+cudaError_t ensure_adj_streams(md_system* s)
+{
+    cudaError_t e = ensure_graph_streams(s);
+    if (e == cudaSuccess && !s->rstream) e = cudaStreamCreateWithFlags(&s->rstream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (!s->ev_rc[k]) e = cudaEventCreateWithFlags(&s->ev_rc[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !s->ev_rev[k]) e = cudaEventCreateWithFlags(&s->ev_rev[k], cudaEventDisableTiming);
+    }
     return e;
 }
 
@@ -934,15 +952,43 @@ struct AdjPlan {
     int K, S, nseg;
 };
 
-size_t carve_adj(const md_system* s, const AdjPlan& P, char* base, AdjView* V)
+// Two sets of segment snapshots: segment k uses set k & 1, so the recompute of segment k-1 can
+// run while segment k is walked back.
+struct AdjSets {
+    float4* pos[2];
+    int32_t* cnt[2];
+    uint32_t* W[2];
+    int32_t* id[2];
+};
+
+// the adjoint view with snapshot set `set` as its snapshot arrays
+AdjView adj_view_of(const AdjView& V, const AdjSets& Z, int set)
+{
+    AdjView v = V;
+    v.pos_snap = Z.pos[set];
+    v.cnt_snap = Z.cnt[set];
+    v.W_snap = Z.W[set];
+    v.id_snap = Z.id[set];
+    return v;
+}
+
+size_t carve_adj(const md_system* s, const AdjPlan& P, char* base, AdjView* V, AdjSets* Z = nullptr)
 {
     Carver c{base};
     AdjView v;
     std::memset(&v, 0, sizeof(v));
+    AdjSets z;
     const size_t ns = size_t(s->plan.nslots), n3 = size_t(s->plan.n_total) * 3;
-    v.pos_snap = c.take<float4>(ns * (P.K + 1));
-    v.cnt_snap = c.take<int32_t>(ns * (P.K + 1));
-    v.W_snap = c.take<uint32_t>(ns * size_t(s->plan.cap) * (P.K + 1));
+    for (int set = 0; set < 2; ++set) {
+        z.pos[set] = c.take<float4>(ns * (P.K + 1));
+        z.cnt[set] = c.take<int32_t>(ns * (P.K + 1));
+        z.W[set] = c.take<uint32_t>(ns * size_t(s->plan.cap) * (P.K + 1));
+        z.id[set] = c.take<int32_t>(ns);
+    }
+    v.pos_snap = z.pos[0];
+    v.cnt_snap = z.cnt[0];
+    v.W_snap = z.W[0];
+    v.id_snap = z.id[0];
     for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 3; ++a) {
             v.lx[b][a] = c.take<double>(ns);
@@ -957,6 +1003,7 @@ size_t carve_adj(const md_system* s, const AdjPlan& P, char* base, AdjView* V)
     v.vnorm_part = c.take<double>(ADJ_VPART);
     v.out = c.take<double>(8);
     if (V) *V = v;
+    if (Z) *Z = z;
     return (c.off + 255) & ~size_t(255);
 }
 
@@ -1008,14 +1055,17 @@ cudaError_t adj_snapshot(md_system* s, const AdjView& V, int q, int cur, cudaStr
     return e;
 }
 
-// The graphs of md_adjoint's segments, captured once per (workspace, horizon, segment shape) and
-// replayed: kind 0 runs `steps` forward steps from buffer 0; kind 1 also snapshots the positions,
-// counts and W before the first and after every step; kind 2 walks the segment back (reverse
-// steps `steps`..1, plus step 0 in the first segment; flags bit 0: the segment ends at the
-// horizon, bit 1: it is the first).  Each step's rebuild sits behind an IF node as in md_integrate.
-int adj_graph(md_system* s, const Scal& Sa, const AdjView& V, const void* work, int nsteps, int ckpt, int kind, int steps,
-              int buf0, int flags, cudaGraphExec_t* out)
+// The graphs of md_adjoint's segments, captured once per (workspace, horizon, segment shape,
+// snapshot set) and replayed: kind 0 runs `steps` forward steps from buffer 0; kind 1 also
+// records the slot -> id map and snapshots the positions, counts and W before the first and after
+// every step; kind 2 walks the segment back (reverse steps `steps`..1, plus step 0 in the first
+// segment; flags bit 0: the segment ends at the horizon, bit 1: it is the first).  Each step's
+// rebuild sits behind an IF node as in md_integrate.
+int adj_graph(md_system* s, const Scal& Sa, const AdjView& V0, const AdjSets& Z, int set, const void* work, int nsteps,
+              int ckpt, int kind, int steps, int buf0, int flags, cudaGraphExec_t* out)
 {
+    const AdjView V = adj_view_of(V0, Z, set);
+    flags |= set << 8;                            // the snapshot set is part of the key
     for (auto& g : s->adj_graphs)
         if (g.work == work && g.nsteps == nsteps && g.ckpt == ckpt && g.kind == kind && g.steps == steps &&
             g.buf0 == buf0 && g.flags == flags) {
@@ -1040,7 +1090,10 @@ int adj_graph(md_system* s, const Scal& Sa, const AdjView& V, const void* work, 
             cudaError_t err = cudaSuccess;
             if (kind == 0 || kind == 1) {
                 int cur = 0;
-                if (kind == 1) err = adj_snapshot(s, V, 0, cur, st);
+                if (kind == 1)                    // the segment's slot -> id map, then snapshot 0
+                    err = cudaMemcpyAsync(V.id_snap, s->A.id, size_t(s->plan.nslots) * sizeof(int32_t),
+                                          cudaMemcpyDeviceToDevice, st);
+                if (kind == 1 && err == cudaSuccess) err = adj_snapshot(s, V, 0, cur, st);
                 for (int q = 1; q <= steps && err == cudaSuccess; ++q) {
                     err = capture_step_and_rebuild(s, Sa, st, cur, false);
                     cur ^= 1;
@@ -1093,7 +1146,8 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
     if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u) || work_bytes < need)
         return fail(MD_ERR_WORKSPACE, "adjoint workspace missing, misaligned or below " + std::to_string(need) + " bytes");
     AdjView V;
-    carve_adj(s, P, static_cast<char*>(d_work), &V);
+    AdjSets Z;
+    carve_adj(s, P, static_cast<char*>(d_work), &V, &Z);
     if (s->binned_fresh) {
         GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
         s->binned_fresh = false;
@@ -1113,7 +1167,7 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
         if (rc) return rc;
         const int steps = std::min(P.K, P.S - k * P.K);
         cudaGraphExec_t g = nullptr;
-        rc = adj_graph(s, Sa, V, d_work, nsteps, ckpt_every, 0, steps, 0, 0, &g);
+        rc = adj_graph(s, Sa, V, Z, 0, d_work, nsteps, ckpt_every, 0, steps, 0, 0, &g);
         if (!rc) rc = replay(s, g);
         if (rc) return rc;
         rc = adj_save(s, Sa, steps & 1, V.ck_x + n3 * (k + 1), V.ck_v + n3 * (k + 1));
@@ -1122,21 +1176,34 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
     // terminal conditions and the |v_S|^2 part of the loss
     GBMD_CUDA(launch_adj_init(V, s->L, s->plan.n_total, V.ck_v + n3 * P.nseg));
     GBMD_CUDA(cudaMemsetAsync(V.tile_acc, 0, sizeof(double) * 4 * size_t(s->plan.ntiles), st));
-    // reverse, one segment at a time: recompute it from its checkpoint, then walk back
+    // reverse, one segment at a time: recompute it from its checkpoint into snapshot set k & 1 (on
+    // the system's stream), then walk it back on the reverse stream, so the recompute of segment
+    // k-1 overlaps the walk of segment k; a set is refilled only after its previous walk ended
+    GBMD_CUDA(ensure_adj_streams(s));
+    GBMD_CUDA(cudaEventRecord(s->ev_rc[0], st));          // the terminal conditions are in place
+    GBMD_CUDA(cudaStreamWaitEvent(s->rstream, s->ev_rc[0], 0));
+    bool set_used[2] = {false, false};
     int buf = 0;
     for (int k = P.nseg - 1; k >= 0; --k) {
+        const int set = k & 1;
+        if (set_used[set]) GBMD_CUDA(cudaStreamWaitEvent(st, s->ev_rev[set], 0));
         rc = adj_load(s, Sa, V.ck_x + n3 * k, V.ck_v + n3 * k);
         if (rc) return rc;
         const int steps = std::min(P.K, P.S - k * P.K);
         const int flags = (k == P.nseg - 1 ? 1 : 0) | (k == 0 ? 2 : 0);
         cudaGraphExec_t gr = nullptr, gb = nullptr;
-        rc = adj_graph(s, Sa, V, d_work, nsteps, ckpt_every, 1, steps, 0, 0, &gr);
+        rc = adj_graph(s, Sa, V, Z, set, d_work, nsteps, ckpt_every, 1, steps, 0, 0, &gr);
         if (!rc) rc = replay(s, gr);
-        if (!rc) rc = adj_graph(s, Sa, V, d_work, nsteps, ckpt_every, 2, steps, buf, flags, &gb);
-        if (!rc) rc = replay(s, gb);
+        if (!rc) rc = adj_graph(s, Sa, V, Z, set, d_work, nsteps, ckpt_every, 2, steps, buf, flags, &gb);
         if (rc) return rc;
+        GBMD_CUDA(cudaEventRecord(s->ev_rc[set], st));
+        GBMD_CUDA(cudaStreamWaitEvent(s->rstream, s->ev_rc[set], 0));
+        GBMD_CUDA(cudaGraphLaunch(gb, s->rstream));
+        GBMD_CUDA(cudaEventRecord(s->ev_rev[set], s->rstream));
+        set_used[set] = true;
         buf ^= (steps + (k == 0 ? 1 : 0)) & 1;
     }
+    GBMD_CUDA(cudaStreamWaitEvent(st, s->ev_rev[0], 0));   // segment 0 (set 0) is walked last
     GBMD_CUDA(launch_adj_final(V, s->L, s->plan.ntiles));
     double out[8];
     GBMD_CUDA(cudaMemcpyAsync(out, V.out, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));

@@ -150,6 +150,7 @@ struct AdjView {
     float4* pos_snap;         // [K+1][nslots] positions of the segment's steps
     int32_t* cnt_snap;        // [K+1][nslots] neighbour counts
     uint32_t* W_snap;         // [K+1][cap][nslots] neighbour matrices
+    int32_t* id_snap;         // [nslots] permanent id of each slot during the segment
     double* lx[2][3];         // adjoint of positions, slot order, ping-pong
     double* lv[2][3];         // adjoint of velocities
     double* mu[2][3];         // kappa (lv + dt lx) of the reverse step that reads buffer b

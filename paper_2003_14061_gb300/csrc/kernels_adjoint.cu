@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView 
     }
 }
 
-// adjoint vectors between id order (kept across segments) and this segment's slot order
+// adjoint vectors between id order (kept across segments) and this segment's slot order (the
+// segment's slot -> id map is a snapshot, so the next segment may already be re-binned)
 // (to slot order, also mu = kappa (lv + dt lx) for the segment's first reverse step)
 __global__ void __launch_bounds__(TILE) k_adj_to_slot(Arrays A, Scal S, AdjView V, int buf, double kappa)
 {
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(TILE) k_adj_to_slot(Arrays A, Scal S, AdjView 
         const Rep& R = A.rep[A.tile_rep[t]];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         if (slot - R.slot0 >= R.n) continue;
-        const int64_t id = A.id[slot];
+        const int64_t id = V.id_snap[slot];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double lx = V.lam_x[id * 3 + a], lv = V.lam_v[id * 3 + a];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(TILE) k_adj_to_id(Arrays A, Scal S, AdjView V,
         const Rep& R = A.rep[A.tile_rep[t]];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         if (slot - R.slot0 >= R.n) continue;
-        const int64_t id = A.id[slot];
+        const int64_t id = V.id_snap[slot];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             V.lam_x[id * 3 + a] = V.lx[buf][a][slot];
