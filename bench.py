@@ -465,7 +465,7 @@ def run_reference(args):
     value = x.shape[0] * args.steps / secs
     sample = f"fcc {ncell}^3 = {x.shape[0]} atoms of the same recipe, {args.steps} steps"
     return {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "device": "host cores (the FP64 oracle)",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "atoms": x.shape[0]},
