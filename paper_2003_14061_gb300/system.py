@@ -208,7 +208,8 @@ class MDSystem:
     def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0,
                    step_kernel: int = 0):
         """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct;
-        step_kernel: 1 = per-thread loads with L2 prefetch, 2 = bulk-copy shared-memory ring."""
+        step_kernel: 1 = per-thread loads with L2 prefetch, 2 = bulk-copy shared-memory ring,
+        3 = staged cell-row windows in shared memory."""
         t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph), int(step_kernel))
         self._call("md_set_tuning", ctypes.byref(t))
 
