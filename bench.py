@@ -311,8 +311,8 @@ def run_gb300(args, rank, world, local_rank):
                        "cuda_graph": graph_mode},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (lambda b: None if b is None else b * n)(traffic_per_atom("k_step<MD_MIXED>")),
-                         "kernel": "k_step<MD_MIXED>",
+                         "traffic": (lambda b: None if b is None else b * n)(traffic_per_atom("k_step_sm<MD_MIXED>")),
+                         "kernel": "k_step_sm<MD_MIXED>",
                          "bytes_per_atom": bpa, "peak_kind": peak_kind},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 48.0 * total_atoms / e2e_steps,

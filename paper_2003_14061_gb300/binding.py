@@ -46,7 +46,7 @@ class md_params(ctypes.Structure):
                 ("skin", ctypes.c_double), ("dt", ctypes.c_double), ("shift_energy", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("reorder_every", ctypes.c_int32),
                 ("nbr_capacity", ctypes.c_int32), ("rebuild_rule", ctypes.c_int32),
-                ("props_every", ctypes.c_int32)]
+                ("props_every", ctypes.c_int32), ("cell_block", ctypes.c_int32)]
 
 
 class md_props(ctypes.Structure):

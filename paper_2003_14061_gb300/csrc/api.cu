@@ -67,8 +67,8 @@ int check_params(const md_params* p)
     if (p->precision < MD_FP64 || p->precision > MD_FP32) return fail(MD_ERR_INVALID_ARG, "bad precision");
     if (p->rebuild_rule < MD_REBUILD_VMAX || p->rebuild_rule > MD_REBUILD_EVERY)
         return fail(MD_ERR_INVALID_ARG, "bad rebuild_rule");
-    if (p->reorder_every < 0 || p->nbr_capacity < 0 || p->props_every < 0)
-        return fail(MD_ERR_INVALID_ARG, "reorder_every, nbr_capacity and props_every must be >= 0");
+    if (p->reorder_every < 0 || p->nbr_capacity < 0 || p->props_every < 0 || p->cell_block < 0)
+        return fail(MD_ERR_INVALID_ARG, "reorder_every, nbr_capacity, props_every and cell_block must be >= 0");
     return MD_OK;
 }
 
@@ -104,6 +104,7 @@ int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const doub
             R.wf[a] = float(R.w[a]);
             nc_tot *= R.nc[a];
         }
+        R.kz = p->cell_block > 0 ? std::min(p->cell_block, R.nc[2]) : 0;   // 0: chosen in md_create
         R.n = int32_t(n_rep[r]);
         R.slot0 = slot;
         R.tile0 = int32_t(slot / TILE);
@@ -187,6 +188,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.props = c.take<md_props>(size_t(P.nrep));
     a.series = c.take<double>(size_t(P.nrep) * P.series_cap * SERIES_COLS);
     a.g = c.take<Global>(1);
+    a.sm_claim = c.take<int32_t>(size_t(SM_RANGES) + 1);
     for (int q = 0; q < 3; ++q) a.xchg[q] = c.take<double>(size_t(P.n_total) * 3);
     if (A) *A = a;
     return (c.off + 255) & ~size_t(255);
@@ -622,6 +624,15 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     cudaError_t e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
     s->nsm = prop.multiProcessorCount;
+    // blocks of the cell order: about sqrt(rows of cells per SM's slot range) planes, at most 8
+    // (measured on the 4M-atom WCA fluid: 4 and 8 equally fast, 12 slower, 1 slowest)
+    for (Rep& R : s->plan.reps) {
+        if (R.kz > 0) continue;
+        const double rows = double(R.nc[1]) * double(R.nc[2]);
+        const double per_range = double(s->plan.nslots) / double(std::max(1, s->nsm)) * rows / double(R.n);
+        const int kz = int(std::lround(std::sqrt(per_range)));
+        R.kz = std::max(1, std::min(std::min(kz, 8), int(R.nc[2])));
+    }
     s->smem_per_sm = int(prop.sharedMemPerMultiprocessor);
     s->smem_per_cta = int(prop.sharedMemPerBlockOptin);
     s->tune.ctas_per_sm = 12;

@@ -26,6 +26,7 @@ namespace gbmd {
 
 constexpr int TILE = 128;                 // slots per tile
 constexpr int NPROP = 8;                  // U, K, W, px, py, pz, (spare), vmax^2
+constexpr int SM_RANGES = 256;            // slot ranges of the step kernel's per-SM schedule
 constexpr int SERIES_COLS = 9;            // step, U, K, W, P, px, py, pz, vmax
 constexpr int IDX_SHIFT = 6;              // W entry: slot << 6 | (o_z+1) << 4 | (o_y+1) << 2 | (o_x+1)
 constexpr int64_t MAX_SLOTS = int64_t(1) << 26;
@@ -45,7 +46,7 @@ struct Rep {                  // per replica, fixed after creation
     int32_t ncells;
     int32_t id0;              // first permanent id
     int32_t nc[3];            // cells per axis
-    int32_t pad;
+    int32_t kz;               // z planes per block of the cell order (1: rows in plain (z, y) order)
     double L[3];              // box sides
     double w[3];              // cell sides L / n_c
     double s[3];              // n_c / L
@@ -121,6 +122,7 @@ struct Arrays {
     md_props* props;          // per replica, output of the props reduction
     double* series;           // [nrep][series_cap][SERIES_COLS]
     Global* g;
+    int32_t* sm_claim;        // [SM_RANGES] warp-tiles claimed per range in this step, then warps done
     // id-ordered exchange buffers (3 doubles per atom)
     double* xchg[3];
 };
@@ -169,6 +171,34 @@ struct AdjView {
 __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz)
 {
     return uint32_t(cx) | (uint32_t(cy) << 10) | (uint32_t(cz) << 20);
+}
+
+// Cell order.  Cells are numbered x fastest, so each row of cells (fixed y, z) is a contiguous
+// run of the cell-ordered arrays.  The rows go in blocks of kz planes, ordered (z / kz, y, z % kz),
+// so that a contiguous range of cells (and of slots, after a reorder) is compact along all three
+// axes; kz = 1 is the plain (z, y) row order.
+__device__ __forceinline__ int row_pos(const Rep& R, int ny, int nz)
+{
+    const int z0 = (nz / R.kz) * R.kz;
+    const int hb = min(R.kz, R.nc[2] - z0);
+    return z0 * R.nc[1] + ny * hb + (nz - z0);
+}
+
+__device__ __forceinline__ int cell_index(const Rep& R, int cx, int cy, int cz)
+{
+    return R.cell0 + row_pos(R, cy, cz) * R.nc[0] + cx;
+}
+
+// (cx, cy, cz) of the replica-local cell number cl
+__device__ __forceinline__ void cell_coords(const Rep& R, int cl, int& cx, int& cy, int& cz)
+{
+    cx = cl % R.nc[0];
+    const int p = cl / R.nc[0];
+    const int z0 = (p / (R.kz * R.nc[1])) * R.kz;
+    const int hb = min(R.kz, R.nc[2] - z0);
+    const int rel = p - z0 * R.nc[1];
+    cy = rel / hb;
+    cz = z0 + rel % hb;
 }
 
 __device__ __forceinline__ void unpack_cell(uint32_t p, int& cx, int& cy, int& cz)

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
             if (MODE != MD_FP32) {
                 A.xl[0][slot] = loc[0]; A.xl[1][slot] = loc[1]; A.xl[2][slot] = loc[2];
             }
-            const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+            const int cell = cell_index(R, c[0], c[1], c[2]);
             A.cell[slot] = cell;
             cell_bin = cell;
         } else if (j < R.n) {
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
                     A.pos32[cur][slot] = make_float4(nl[0], nl[1], nl[2], cell_word_f(pack_cell(c[0], c[1], c[2])));
                 }
             }
-            const int cell = R.cell0 + (c[2] * R.nc[1] + c[1]) * R.nc[0] + c[0];
+            const int cell = cell_index(R, c[0], c[1], c[2]);
             if (moved) A.cell[slot] = cell;
             cell_bin = cell;
         }
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
                                   ((oz < 0) ? dlo2[2] : ((oz > 0) ? dhi2[2] : T(0)));
                     if (dyz > skip2) continue;
                     const bool use_l = dyz + dlo2[0] <= skip2, use_r = dyz + dhi2[0] <= skip2;
-                    const int row = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0];
+                    const int row = R.cell0 + row_pos(R, ny, nz) * R.nc[0];
                     const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
                     // the three cells of this row, as [b0,e0) [b1,e1) [b2,e2) in perm; without a
                     // periodic wrap in x they are one contiguous range [b0, e2) split at b1, b2
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
                                       ((oz < 0) ? dlo2[2] : ((oz > 0) ? dhi2[2] : 0.0f));
                     if (dyz > skip2) continue;
                     const bool use_l = dyz + dlo2[0] <= skip2, use_r = dyz + dhi2[0] <= skip2;
-                    const int row = R.cell0 + (nz * R.nc[1] + ny) * ncx;
+                    const int row = R.cell0 + row_pos(R, ny, nz) * ncx;
                     const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
                     if (inner) {
                         // cells cx-1, cx, cx+1 are adjacent runs [b0,b1) [b1,b2) [b2,b3) of psort
@@ -789,7 +789,8 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
         if (!A.rs[r].rebuild) continue;
         const Rep& R = A.rep[r];
         const int cl = c - R.cell0;
-        const int cx = cl % R.nc[0], cy = (cl / R.nc[0]) % R.nc[1], cz = cl / (R.nc[0] * R.nc[1]);
+        int cx, cy, cz;
+        cell_coords(R, cl, cx, cy, cz);
         const int xs[3] = {(cx == 0) ? R.nc[0] - 1 : cx - 1, cx, (cx == R.nc[0] - 1) ? 0 : cx + 1};
         const float w0 = R.wf[0], w1 = R.wf[1], w2 = R.wf[2];
         const int ab = A.cstart[c], ae = A.cstart[c + 1];
@@ -807,7 +808,7 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
                 int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
                 int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
                 const float dyz = ((oy < 0) ? dl[1] : ((oy > 0) ? dh[1] : 0.f)) + ((oz < 0) ? dl[2] : ((oz > 0) ? dh[2] : 0.f));
-                const int rowc = R.cell0 + (nz * R.nc[1] + ny) * R.nc[0];
+                const int rowc = R.cell0 + row_pos(R, ny, nz) * R.nc[0];
                 Q.tot = 0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {

@@ -10,10 +10,13 @@
 //              Sec. 2.3, an atomic counter after a memory fence) updates the refresh criterion
 //              and raises the rebuild flag.  With PROPS, the tile also writes FP64 partial sums
 //              of U, K, virial and momentum (F2).
+//   k_step_sm  the same for MD_MIXED and MD_FP32 steps without props (step kernel 1): warps take
+//              32-slot warp-tiles from the slot range of the SM they run on, so the warps of an SM
+//              gather from one neighbourhood held in its L1.
 //   k_step<..., STG = true>  the same with each tile's neighbour positions staged in shared
 //              memory by cp.async.bulk first (step kernel 3).
 //   k_step_bulk  the same arithmetic with the tile's state and W rows in a two-stage shared-memory
-//              ring filled by cp.async.bulk (step kernel 2).  The three forms share the pair loop
+//              ring filled by cp.async.bulk (step kernel 2).  The four forms share the pair loop
 //              and the kick-drift, so they give bit-identical trajectories.
 //   k_forces   F1 alone: f_i, u_i and the per-atom virial at the current positions.
 //   k_props_*  F2 and the other measured quantities: per-tile FP64 partials, then one CTA per
@@ -554,6 +557,200 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
 }
 
 // ------------------------------------------------------------------------------------------
+// fused force + leapfrog step on a per-SM schedule (MD_MIXED, MD_FP32; steps without props)
+// ------------------------------------------------------------------------------------------
+// The slots are cut into SM_RANGES-bounded contiguous ranges, one per SM id, and each warp takes
+// 32-slot warp-tiles from the range of the SM it runs on (an atomic counter per range), in
+// order.  All warps of an SM therefore compute neighbouring atoms at the same time, and since
+// slots are in cell order with the rows of cells blocked in z (row_pos), their neighbour
+// gathers share one compact region in the SM's L1 instead of one region per CTA.  A warp whose
+// range is exhausted takes warp-tiles from any range with some left, so every warp-tile is
+// computed exactly once whatever the placement of the CTAs.  The last warp to finish resets the
+// counters for the next step.  Per atom the arithmetic is k_step's, bit for bit.
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Fold one warp's contribution to replica r (k_step's flush_replica for a warp): the maximum of
+// the refresh metric and the number of warp-tiles; the warp that completes the replica's
+// warp-tiles runs the refresh bookkeeping.
+__device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& S, int r, float run_max, int wtiles,
+                                                   cudaGraphConditionalHandle cond, int use_cond)
+{
+    const float m = warp_max(run_max);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&A.rs[r].vmax2, __float_as_uint(m));
+        __threadfence();
+        const int done = atomicAdd(&A.rs[r].tiles_done, wtiles) + wtiles;
+        if (done == A.rep[r].ntiles * (TILE / 32)) {
+            __threadfence();
+            finish_replica_step(A, S, r, cond, use_cond);
+        }
+    }
+    __syncwarp();
+}
+
+template <int MODE, int NB, int MINB>
+__global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
+                                                      int use_cond)
+{
+    static_assert(MODE != MD_FP64, "MD_FP64 steps run k_step");
+    const int nxt = cur ^ 1;
+    const int lane = threadIdx.x & 31;
+    uint32_t smid, nsmid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    const int nr = max(1, min(int(nsmid), SM_RANGES));
+    const int home = int(smid) % nr;
+    const int nwt = S.ntiles * (TILE / 32);
+    const int per = (nwt + nr - 1) / nr;
+    int* const claimc = A.sm_claim;
+    const float4* __restrict__ pos = A.pos32[cur];
+    auto range_len = [&](int q) { return max(0, min(nwt - q * per, per)); };
+
+    bool home_open = true;
+    // a warp-tile of any range with some left, or -1 when all are done.  Every failed claim
+    // leaves its range exhausted for the rest of the launch, so nr + 1 scans always suffice.
+    auto steal = [&]() -> int {
+        for (int iter = 0; iter <= nr + 1; ++iter) {
+            int sel = -1;
+            for (int i = 0; i * 32 < nr && sel < 0; ++i) {
+                const int q = i * 32 + lane;
+                const int rr = (home + 1 + q) % nr;
+                const bool avail = q < nr && ld_relaxed_gpu(claimc + rr) < range_len(rr);
+                const unsigned b = __ballot_sync(0xffffffffu, avail);
+                if (b) sel = (home + 1 + i * 32 + __ffs(b) - 1) % nr;
+            }
+            if (sel < 0) return -1;
+            int k = 0;
+            if (lane == 0) k = atomicAdd(claimc + sel, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k < range_len(sel)) return sel * per + k;
+        }
+        if (lane == 0) atomicOr(&A.g->err, ERR_TIMEOUT);     // unreachable: the scan is bounded
+        return -1;
+    };
+    auto claim_now = [&]() -> int {
+        if (home_open) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(claimc + home, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k < range_len(home)) return home * per + k;
+            home_open = false;
+        }
+        return steal();
+    };
+
+    // w0 is computed while w1, the next warp-tile, has its positions and state prefetched into
+    // L2 and the claim of the one after it is in flight
+    int w0 = claim_now();
+    int w1 = (w0 >= 0) ? claim_now() : -1;
+    int run_r = -1, run_cnt = 0;
+    float run_max = 0.0f;
+    while (w0 >= 0) {
+        int pend = 0;
+        const bool pending = home_open && w1 >= 0;
+        if (pending && lane == 0) pend = atomicAdd(claimc + home, 1);
+        int c1 = 0;
+        if (w1 >= 0) {
+            // one prefetch per 128-byte line: 4 lines of positions, 2 of each FP64 stream (1 of
+            // each FP32 stream), 4 of positions at the last rebuild (rule DISP)
+            const int64_t s1 = int64_t(w1) * 32;
+            constexpr int NSTATE = (MODE == MD_MIXED) ? 12 : 3;
+            const int nref = (S.rule == MD_REBUILD_DISP) ? 4 : 0;
+            if (lane < 4 + NSTATE + nref) {
+                const void* p;
+                if (lane < 4) {
+                    p = A.pos32[cur] + s1 + 8 * lane;
+                } else if (lane < 4 + NSTATE) {
+                    const int q = lane - 4;
+                    if (MODE == MD_MIXED) p = ((q & 1) ? A.v[q >> 2] : A.xl[q >> 2]) + s1 + 16 * ((q >> 1) & 1);
+                    else p = A.v32[q] + s1;
+                } else {
+                    p = A.xref + s1 + 8 * (lane - 4 - NSTATE);
+                }
+                prefetch_l2(p);
+            }
+            c1 = __ldcs(A.nbr_count + s1 + lane);
+        }
+        const int r = A.tile_rep[w0 / (TILE / 32)];
+        if (r != run_r) {
+            if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond);
+            run_r = r;
+            run_cnt = 0;
+            run_max = 0.0f;
+        }
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(w0) * 32 + lane;
+        const bool active = slot - R.slot0 < R.n;
+        const int vhalf = A.rs[r].vhalf;
+        float metric = 0.0f;                     // |v|^2 (VMAX) or |x - x_ref|^2 (DISP)
+        if (active) {
+            const float4 pi = __ldg(pos + slot);
+            const AccF a = force_f32<NB>(A, S, R, pos, slot, pi);
+            double v[3], x[3], part[NPROP];
+            float v32[3], pn[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (MODE == MD_MIXED) {
+                    v[q] = __ldcs(A.v[q] + slot);
+                    x[q] = __ldcs(A.xl[q] + slot);
+                } else {
+                    v32[q] = A.v32[q][slot];
+                }
+            }
+            metric = kick_drift<MODE, false>(S, vhalf, pi, a, v, x, v32, pn, part);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (MODE == MD_MIXED) {
+                    __stcs(A.v[q] + slot, v[q]);
+                    __stcs(A.xl[q] + slot, x[q]);
+                } else {
+                    A.v32[q][slot] = v32[q];
+                }
+            }
+            A.pos32[nxt][slot] = make_float4(pn[0], pn[1], pn[2], pi.w);
+            if (S.rule == MD_REBUILD_DISP) {
+                const float4 xr = A.xref[slot];
+                const float d0 = pn[0] - xr.x, d1 = pn[1] - xr.y, d2 = pn[2] - xr.z;
+                metric = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+            }
+            if (!(metric <= 3.0e38f)) metric = __uint_as_float(0x7f800000u);   // +inf marks non-finite
+        }
+        run_max = fmaxf(run_max, metric);
+        run_cnt += 1;
+        int w2 = -1;
+        if (w1 >= 0) {
+            // the rows of W below the next warp-tile's largest count into L2
+            const int mw = min(__reduce_max_sync(0xffffffffu, unsigned(c1)), unsigned(S.cap));
+            for (int k = lane; k < mw; k += 32) prefetch_l2(A.W + int64_t(k) * S.nslots + int64_t(w1) * 32);
+            if (pending) {
+                const int k = __shfl_sync(0xffffffffu, pend, 0);
+                if (k < range_len(home)) w2 = home * per + k;
+                else home_open = false;
+            }
+            if (w2 < 0 && !home_open) w2 = steal();
+        }
+        w0 = w1;
+        w1 = w2;
+    }
+    if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond);
+    // the last warp of the launch resets the counters; the next launch is ordered after this one
+    if (lane == 0) {
+        __threadfence();
+        const int total = int(gridDim.x) * (TILE / 32);
+        if (atomicAdd(claimc + SM_RANGES, 1) == total - 1) {
+            for (int q = 0; q < nr; ++q) claimc[q] = 0;
+            claimc[SM_RANGES] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // fused force + leapfrog step through a shared-memory ring (MD_MIXED, MD_FP32)
 // ------------------------------------------------------------------------------------------
 // Each CTA takes a contiguous run of tiles and keeps two of them in a two-stage ring in shared
@@ -929,7 +1126,9 @@ __global__ void __launch_bounds__(TILE) k_get_cells(Arrays A, Scal S, int32_t* o
         const Rep& R = A.rep[r];
         const int64_t slot = int64_t(t) * TILE + threadIdx.x;
         if (slot - R.slot0 >= R.n) continue;
-        out[A.id[slot]] = A.cell[slot] - R.cell0;
+        int cx, cy, cz;
+        cell_coords(R, A.cell[slot] - R.cell0, cx, cy, cz);
+        out[A.id[slot]] = (cz * R.nc[1] + cy) * R.nc[0] + cx;
     }
 }
 
@@ -965,7 +1164,10 @@ template <int M, int NB, int MINB, bool STG = false>
 static int occ_of(int dyn_smem = 0)
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<M, false, NB, MINB, STG>, TILE, dyn_smem);
+    if constexpr (M != MD_FP64 && !STG)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, NB, MINB>, TILE, dyn_smem);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<M, false, NB, MINB, STG>, TILE, dyn_smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<M, true, NB, MINB, STG>, TILE, dyn_smem);
     return std::max(1, std::min(a, b));
 }
@@ -1100,9 +1302,12 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
 #define GBMD_STEP(M, NB, MB)                                                                           \
     {                                                                                                  \
         if (props) k_step<M, true, NB, MB, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);  \
-        else k_step<M, false, NB, MB, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);       \
+        else k_step_sm<M, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);                      \
     }
-        if (S.mode == MD_FP64) GBMD_STEP(MD_FP64, 2, 4)
+        if (S.mode == MD_FP64) {
+            if (props) k_step<MD_FP64, true, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);
+            else k_step<MD_FP64, false, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);
+        }
         else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
         else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)
 #undef GBMD_STEP

@@ -20,7 +20,7 @@ WCA_RC = 2.0 ** (1.0 / 6.0)
 
 def make_params(*, eps=1.0, sigma=1.0, mass=1.0, rc=WCA_RC, skin=0.4, dt=0.005, shift=True,
                 precision="mixed", reorder_every=100, nbr_capacity=0, rebuild_rule="vmax",
-                props_every=0, n=0, box=(1.0, 1.0, 1.0)) -> B.md_params:
+                props_every=0, cell_block=0, n=0, box=(1.0, 1.0, 1.0)) -> B.md_params:
     p = B.md_params()
     p.n = int(n)
     for a in range(3):
@@ -32,6 +32,7 @@ def make_params(*, eps=1.0, sigma=1.0, mass=1.0, rc=WCA_RC, skin=0.4, dt=0.005, 
     p.nbr_capacity = int(nbr_capacity)
     p.rebuild_rule = _RULE[rebuild_rule] if isinstance(rebuild_rule, str) else int(rebuild_rule)
     p.props_every = int(props_every)
+    p.cell_block = int(cell_block)
     return p
 
 

@@ -170,6 +170,51 @@ def test_launch_shapes_do_not_change_results():
         assert np.array_equal(x, xr) and np.array_equal(v, vr), (ctas, nb, bb, sk)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("block", [3, 4])
+@pytest.mark.parametrize("name", ["wca2048", "ortho"])
+def test_blocked_cell_order_matches_oracle(name, prec, block):
+    # rows of cells numbered in blocks of 3 or 4 z planes (8 planes: a short last block for 3):
+    # cell ids (reported in the plain order), neighbour sets and, on the fluid that
+    # test_trajectory_100_steps runs, a 100-step trajectory agree with the oracle as with the
+    # plain order
+    s, x, v, box, rc, skin = make(name, prec, cell_block=block)
+    nc, cell = oracle.cells(x, box, rc + skin)
+    assert nc[2] == 8
+    assert np.array_equal(s.cells(), cell)
+    s.build_neighbours()
+    counts, nb = s.neighbours()
+    _, oc, off, onb = oracle.neighbours(x, box, rc, skin, fp32=(prec != "fp64"))
+    assert np.array_equal(counts, oc)
+    for i in range(x.shape[0]):
+        assert np.array_equal(np.sort(nb[i, : counts[i]]), onb[off[i]: off[i + 1]]), i
+    if name != "wca2048":
+        return
+    s.integrate(100)
+    xg, vg, _ = s.state()
+    xo, vo, po, _ = oracle.run(x, v, box, oracle.pot(rc=rc), dt=0.005, nsteps=100, rule=1, skin=skin)
+    assert np.abs(min_image(xg - xo, box)).max() <= 1e-4
+    assert rel_l2(vg, vo) <= 1e-4
+    assert abs(s.props()[0]["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / x.shape[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("rule", ["vmax", "disp"])
+def test_sm_schedule_matches_tile_schedule(prec, rule):
+    # steps without props run the per-SM warp-tile schedule (k_step_sm), steps with props the
+    # per-CTA tile schedule (k_step): the same arithmetic per atom, so the trajectories and the
+    # rebuild counts agree bit for bit, here with the cell order blocked in z as well
+    out = []
+    for pe in (0, 1):
+        s, *_ = make("wca2048", prec, rebuild_rule=rule, props_every=pe, cell_block=3)
+        s.integrate(120)
+        x, v, _ = s.state()
+        out.append((x, v, s.props()[0]["rebuilds"]))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp32"])
 @pytest.mark.parametrize("rule", ["vmax", "disp"])
 @pytest.mark.parametrize("ctas", [2, 8])
