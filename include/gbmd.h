@@ -206,10 +206,13 @@ typedef struct {
                                 atoms) */
     int32_t use_graph;       /* 1: md_integrate replays captured CUDA graphs; 2: direct launches */
     int32_t step_kernel;     /* fused step kernel (MD_MIXED, MD_FP32): 1 = each thread loads its
-                                atom's state and W column, the next tile prefetched into L2;
+                                atom's state and W column; warps take 32-atom warp-tiles from
+                                the slot range of the SM they run on, the next one prefetched
+                                into L2;
                                 2 = the tile's state and W rows copied into a two-stage
                                 shared-memory ring by cp.async.bulk, completing on mbarriers;
-                                3 = as 1, with each tile's neighbour positions first copied into
+                                3 = as 1 but on 128-atom tiles per CTA, with each tile's
+                                neighbour positions first copied into
                                 shared memory by cp.async.bulk (one slot window per row of
                                 neighbour cells; compact when atoms are reordered at every
                                 rebuild, reorder_every = 0) */

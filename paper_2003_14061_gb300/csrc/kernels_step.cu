@@ -10,9 +10,9 @@
 //              Sec. 2.3, an atomic counter after a memory fence) updates the refresh criterion
 //              and raises the rebuild flag.  With PROPS, the tile also writes FP64 partial sums
 //              of U, K, virial and momentum (F2).
-//   k_step_sm  the same for MD_MIXED and MD_FP32 steps without props (step kernel 1): warps take
-//              32-slot warp-tiles from the slot range of the SM they run on, so the warps of an SM
-//              gather from one neighbourhood held in its L1.
+//   k_step_sm  the same for MD_MIXED and MD_FP32 (step kernel 1): warps take 32-slot warp-tiles
+//              from the slot range of the SM they run on, so the warps of an SM gather from one
+//              neighbourhood held in its L1.  k_step runs MD_FP64 and step kernel 3.
 //   k_step<..., STG = true>  the same with each tile's neighbour positions staged in shared
 //              memory by cp.async.bulk first (step kernel 3).
 //   k_step_bulk  the same arithmetic with the tile's state and W rows in a two-stage shared-memory
@@ -231,10 +231,12 @@ __device__ __forceinline__ float tile_max(float v, float* sh)
 // quantities a lane carries, 4 + 2 + 1 adds, then 2 more over the last 4 lanes): 9 FP64 adds per
 // lane instead of 35 for a butterfly per quantity (FP64 runs at 1/64-1/72 of the FP32 rate on
 // GB300).
-__device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[NPROP], double* out)
+// The in-warp part: lane 4q (q < NPROP - 1) ends with the warp's sum of quantity q, lane 0 also
+// with the warp's maximum of |v|^2 (returned in vm).
+__device__ __forceinline__ double warp_partials(double (&p)[NPROP], int& q, float& vm)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float vm = warp_max(float(p[NPROP - 1]));
+    const int lane = threadIdx.x & 31;
+    vm = warp_max(float(p[NPROP - 1]));
     p[NPROP - 1] = 0.0;
     const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
     double a4[4];
@@ -252,16 +254,34 @@ __device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[N
     double a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
     a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
     a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-    const int q = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
-    if ((lane & 3) == 0 && q != NPROP - 1) sh[warp][q] = a1;
-    if (lane == 0) sh[warp][NPROP - 1] = double(vm);
+    q = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
+    return a1;
+}
+
+// the NPROP values of one warp into dst[0..NPROP)
+__device__ __forceinline__ void warp_partials_store(double (&p)[NPROP], double* dst)
+{
+    const int lane = threadIdx.x & 31;
+    int q;
+    float vm;
+    const double a1 = warp_partials(p, q, vm);
+    if ((lane & 3) == 0 && q != NPROP - 1) dst[q] = a1;
+    if (lane == 0) dst[NPROP - 1] = double(vm);
+}
+
+// the tile's value of quantity k from its warps' values, in warp order
+__device__ __forceinline__ double combine_warps(const double* w, int k, int stride)
+{
+    double s = w[k];
+    for (int j = 1; j < TILE / 32; ++j) s = (k == NPROP - 1) ? fmax(s, w[j * stride + k]) : s + w[j * stride + k];
+    return s;
+}
+
+__device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[NPROP], double* out)
+{
+    warp_partials_store(p, sh[threadIdx.x >> 5]);
     __syncthreads();
-    if (threadIdx.x < NPROP) {
-        const int k = threadIdx.x;
-        double s = sh[0][k];
-        for (int w = 1; w < TILE / 32; ++w) s = (k == NPROP - 1) ? fmax(s, sh[w][k]) : s + sh[w][k];
-        out[k] = s;
-    }
+    if (threadIdx.x < NPROP) out[threadIdx.x] = combine_warps(&sh[0][0], threadIdx.x, NPROP);
 }
 
 // Refresh criterion and step bookkeeping, run by one thread of the CTA that completed the last
@@ -557,7 +577,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
 }
 
 // ------------------------------------------------------------------------------------------
-// fused force + leapfrog step on a per-SM schedule (MD_MIXED, MD_FP32; steps without props)
+// fused force + leapfrog step on a per-SM schedule (MD_MIXED, MD_FP32)
 // ------------------------------------------------------------------------------------------
 // The slots are cut into SM_RANGES-bounded contiguous ranges, one per SM id, and each warp takes
 // 32-slot warp-tiles from the range of the SM it runs on (an atomic counter per range), in
@@ -566,7 +586,9 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
 // gathers share one compact region in the SM's L1 instead of one region per CTA.  A warp whose
 // range is exhausted takes warp-tiles from any range with some left, so every warp-tile is
 // computed exactly once whatever the placement of the CTAs.  The last warp to finish resets the
-// counters for the next step.  Per atom the arithmetic is k_step's, bit for bit.
+// counters for the next step.  Per atom the arithmetic is k_step's, bit for bit, and so are the
+// props: each warp stores its partial sums and the last of a tile's four warps adds them up in
+// warp order, as k_step's tile reduction does.
 __device__ __forceinline__ int ld_relaxed_gpu(const int* p)
 {
     int v;
@@ -593,7 +615,7 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
     __syncwarp();
 }
 
-template <int MODE, int NB, int MINB>
+template <int MODE, bool PROPS, int NB, int MINB>
 __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                       int use_cond)
 {
@@ -676,7 +698,8 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
             }
             c1 = __ldcs(A.nbr_count + s1 + lane);
         }
-        const int r = A.tile_rep[w0 / (TILE / 32)];
+        const int t = w0 / (TILE / 32);
+        const int r = A.tile_rep[t];
         if (r != run_r) {
             if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond);
             run_r = r;
@@ -688,10 +711,13 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         const bool active = slot - R.slot0 < R.n;
         const int vhalf = A.rs[r].vhalf;
         float metric = 0.0f;                     // |v|^2 (VMAX) or |x - x_ref|^2 (DISP)
+        double part[NPROP];
+#pragma unroll
+        for (int q = 0; q < NPROP; ++q) part[q] = 0.0;
         if (active) {
             const float4 pi = __ldg(pos + slot);
             const AccF a = force_f32<NB>(A, S, R, pos, slot, pi);
-            double v[3], x[3], part[NPROP];
+            double v[3], x[3];
             float v32[3], pn[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -702,7 +728,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
                     v32[q] = A.v32[q][slot];
                 }
             }
-            metric = kick_drift<MODE, false>(S, vhalf, pi, a, v, x, v32, pn, part);
+            metric = kick_drift<MODE, PROPS>(S, vhalf, pi, a, v, x, v32, pn, part);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 if (MODE == MD_MIXED) {
@@ -722,6 +748,30 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         }
         run_max = fmaxf(run_max, metric);
         run_cnt += 1;
+        if (PROPS) {
+            // the warp's partials; the tile's fourth warp to store them sums the four in warp
+            // order, as k_step's tile reduction does, so the props agree bit for bit
+            warp_partials_store(part, A.warp_part + int64_t(w0) * NPROP);
+            __threadfence();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(A.tile_warps + t, 1) == TILE / 32 - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                if (lane < NPROP) {
+                    const double* wp = A.warp_part + int64_t(t) * (TILE / 32) * NPROP;
+                    double y = __ldcg(wp + lane);
+#pragma unroll
+                    for (int j = 1; j < TILE / 32; ++j) {
+                        const double z = __ldcg(wp + j * NPROP + lane);
+                        y = (lane == NPROP - 1) ? fmax(y, z) : y + z;      // combine_warps' order
+                    }
+                    A.tile_part[int64_t(t) * NPROP + lane] = y;
+                }
+                if (lane == 0) A.tile_warps[t] = 0;
+            }
+        }
         int w2 = -1;
         if (w1 >= 0) {
             // the rows of W below the next warp-tile's largest count into L2
@@ -1164,11 +1214,13 @@ template <int M, int NB, int MINB, bool STG = false>
 static int occ_of(int dyn_smem = 0)
 {
     int a = 0, b = 0;
-    if constexpr (M != MD_FP64 && !STG)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, NB, MINB>, TILE, dyn_smem);
-    else
+    if constexpr (M != MD_FP64 && !STG) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, false, NB, MINB>, TILE, dyn_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_sm<M, true, NB, MINB>, TILE, dyn_smem);
+    } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step<M, false, NB, MINB, STG>, TILE, dyn_smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<M, true, NB, MINB, STG>, TILE, dyn_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<M, true, NB, MINB, STG>, TILE, dyn_smem);
+    }
     return std::max(1, std::min(a, b));
 }
 
@@ -1301,8 +1353,8 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
     } else {
 #define GBMD_STEP(M, NB, MB)                                                                           \
     {                                                                                                  \
-        if (props) k_step<M, true, NB, MB, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);  \
-        else k_step_sm<M, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);                      \
+        if (props) k_step_sm<M, true, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);         \
+        else k_step_sm<M, false, NB, MB><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);               \
     }
         if (S.mode == MD_FP64) {
             if (props) k_step<MD_FP64, true, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);

@@ -200,10 +200,10 @@ def test_blocked_cell_order_matches_oracle(name, prec, block):
 
 @pytest.mark.parametrize("prec", ["mixed", "fp32"])
 @pytest.mark.parametrize("rule", ["vmax", "disp"])
-def test_sm_schedule_matches_tile_schedule(prec, rule):
-    # steps without props run the per-SM warp-tile schedule (k_step_sm), steps with props the
-    # per-CTA tile schedule (k_step): the same arithmetic per atom, so the trajectories and the
-    # rebuild counts agree bit for bit, here with the cell order blocked in z as well
+def test_props_steps_do_not_change_the_trajectory(prec, rule):
+    # steps that reduce the props (every step here) and steps that do not run the same
+    # arithmetic per atom: trajectories and rebuild counts agree bit for bit, here with the cell
+    # order blocked in z
     out = []
     for pe in (0, 1):
         s, *_ = make("wca2048", prec, rebuild_rule=rule, props_every=pe, cell_block=3)
