@@ -395,6 +395,8 @@ int apply_tuning(md_system* s)
 {
     const int per_sm = std::max(1, s->tune.ctas_per_sm);
     s->L.grid = std::max(1, s->nsm * per_sm);
+    s->L.nsm = std::max(1, s->nsm);
+    prime_rebuild_grids(s->S, s->L);
     s->L.step_block = TILE;
     s->L.build_block = TILE;
     s->L.nbr_batch = s->tune.nbr_batch;

@@ -396,6 +396,7 @@ __host__ __device__ inline StageLayout stage_layout(int mode, int rows)
 struct Launch {
     cudaStream_t stream;
     int grid;                 // persistent CTAs for tile loops
+    int nsm;                  // SMs of the device
     int grid_step;            // persistent CTAs of the step kernel (capped at its occupancy)
     int step_block;
     int build_block;
@@ -418,6 +419,7 @@ int set_last_error(int code, const char* msg);
 
 // rebuild path (kernels_rebuild.cu)
 cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder);
+void prime_rebuild_grids(const Scal& S, const Launch& L);
 cudaError_t launch_rebuild(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
 cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);
 cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set);   // 7 kernels

@@ -1043,6 +1043,36 @@ static int tile_grid(const Scal& S, const Launch& L)
     return std::max(1, std::min(L.grid, S.ntiles));
 }
 
+// Grid of a per-tile rebuild kernel that holds nothing across tiles (binning, scatter, reorder):
+// every CTA the device can keep resident, since each adds memory requests in flight and these
+// kernels wait on memory and atomics.  The occupancy of each kernel is looked up once.
+template <auto Kernel>
+static int resident_grid(const Scal& S, const Launch& L)
+{
+    static const int per_sm = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, Kernel, TILE, 0) != cudaSuccess) b = 0;
+        return b;
+    }();
+    const int g = (per_sm > 0) ? L.nsm * per_sm : L.grid;
+    return std::max(1, std::min(g, S.ntiles));
+}
+
+// looks the occupancies up outside any stream capture
+void prime_rebuild_grids(const Scal& S, const Launch& L)
+{
+    (void)resident_grid<k_bin<MD_FP64>>(S, L);
+    (void)resident_grid<k_bin<MD_MIXED>>(S, L);
+    (void)resident_grid<k_bin<MD_FP32>>(S, L);
+    (void)resident_grid<k_scatter>(S, L);
+    (void)resident_grid<k_reorder_gather<MD_FP64>>(S, L);
+    (void)resident_grid<k_reorder_gather<MD_MIXED>>(S, L);
+    (void)resident_grid<k_reorder_gather<MD_FP32>>(S, L);
+    (void)resident_grid<k_reorder_copy<MD_FP64>>(S, L);
+    (void)resident_grid<k_reorder_copy<MD_MIXED>>(S, L);
+    (void)resident_grid<k_reorder_copy<MD_FP32>>(S, L);
+}
+
 cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder)
 {
     k_force_rebuild<<<1, 256, 0, L.stream>>>(A, S, reorder);
@@ -1051,15 +1081,15 @@ cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L
 
 cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, int cur, bool from_set)
 {
-    const int g = tile_grid(S, L);
     k_rebuild_list<<<1, 1024, 0, L.stream>>>(A, S);
-    if (S.mode == MD_FP64) k_bin<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
-    else if (S.mode == MD_MIXED) k_bin<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
-    else k_bin<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur, from_set ? 1 : 0);
+    const int fs = from_set ? 1 : 0;
+    if (S.mode == MD_FP64) k_bin<MD_FP64><<<resident_grid<k_bin<MD_FP64>>(S, L), TILE, 0, L.stream>>>(A, S, cur, fs);
+    else if (S.mode == MD_MIXED) k_bin<MD_MIXED><<<resident_grid<k_bin<MD_MIXED>>(S, L), TILE, 0, L.stream>>>(A, S, cur, fs);
+    else k_bin<MD_FP32><<<resident_grid<k_bin<MD_FP32>>(S, L), TILE, 0, L.stream>>>(A, S, cur, fs);
     k_scan_chunks<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
     k_scan_top<<<1, 1024, 0, L.stream>>>(A, S);
     k_scan_apply<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
-    k_scatter<<<g, TILE, 0, L.stream>>>(A, S);
+    k_scatter<<<resident_grid<k_scatter>(S, L), TILE, 0, L.stream>>>(A, S);
     const int gs = int(std::min<int64_t>((S.ncells + 255) / 256, int64_t(L.grid) * 8));
     k_sort_cells<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S, cur);
     return cudaGetLastError();
@@ -1067,17 +1097,15 @@ cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, in
 
 cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur)
 {
-    const int g = tile_grid(S, L);
-    if (S.mode == MD_FP64) {
-        k_reorder_gather<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
-        k_reorder_copy<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    } else if (S.mode == MD_MIXED) {
-        k_reorder_gather<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);
-        k_reorder_copy<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);
-    } else {
-        k_reorder_gather<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur);
-        k_reorder_copy<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur);
+#define GBMD_REORDER(M)                                                                               \
+    {                                                                                                 \
+        k_reorder_gather<M><<<resident_grid<k_reorder_gather<M>>(S, L), TILE, 0, L.stream>>>(A, S, cur); \
+        k_reorder_copy<M><<<resident_grid<k_reorder_copy<M>>(S, L), TILE, 0, L.stream>>>(A, S, cur);     \
     }
+    if (S.mode == MD_FP64) GBMD_REORDER(MD_FP64)
+    else if (S.mode == MD_MIXED) GBMD_REORDER(MD_MIXED)
+    else GBMD_REORDER(MD_FP32)
+#undef GBMD_REORDER
     return cudaGetLastError();
 }
 
