@@ -358,6 +358,19 @@ def test_batched_replicas(prec):
         off += n
 
 
+@pytest.mark.parametrize("build", [2, 32])
+def test_neighbour_overflow_on_rebuild_is_reported(build):
+    # atoms pushed into one octant: eight times the density the capacity was sized for
+    x, box, rc, skin, T = case("wca1372")
+    v = inputs.maxwell(x.shape[0], T, seed=5)
+    s = MDSystem(x, v, box, rc=rc, skin=skin)
+    s.set_tuning(build_batch=build)
+    with pytest.raises(B.MDError) as e:
+        s.set_state(x * 0.5, v)
+        s.check()
+    assert e.value.status == "MD_ERR_NBR_OVERFLOW"
+
+
 def test_neighbour_overflow_is_reported():
     x, box, rc, skin, T = case("wca1372")
     v = inputs.maxwell(x.shape[0], T, seed=5)
