@@ -85,10 +85,11 @@ typedef struct {
     int32_t rebuild_rule;  /* md_rebuild_rule */
     int32_t props_every;   /* >0: accumulate props every this many steps inside md_integrate into
                               a device time series (md_get_series); 0: only on md_reduce_props */
-    int32_t cell_block;    /* cell order: rows of cells (fixed y, z) are numbered in blocks of this
-                              many z planes, (z / b, y, z % b), x fastest within a row, so that
-                              slot ranges are compact in 3D; 1 = plain (z, y) order, 0 = chosen
-                              from the system size and the SM count.  Performance only: results
+    int32_t cell_block;    /* cell order: rows of cells (fixed y, z) are numbered in blocks of b z
+                              planes, (z / b, y, z % b), x fastest within a row, so that slot
+                              ranges are compact in 3D; b = this value rounded down to a power of
+                              two; 1 = plain (z, y) order, 0 = chosen from the system size and
+                              the SM count.  Performance only: results
                               agree with any other choice to rounding (the summation order of a
                               force follows the within-cell order), cells and neighbour sets
                               exactly. */

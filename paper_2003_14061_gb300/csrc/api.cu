@@ -72,6 +72,14 @@ int check_params(const md_params* p)
     return MD_OK;
 }
 
+// the largest power of two not above v (v >= 1)
+int pow2_floor(int v)
+{
+    int k = 1;
+    while (2 * k <= v) k *= 2;
+    return k;
+}
+
 int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const double* box_rep, Plan* P)
 {
     int rc = check_params(p);
@@ -104,7 +112,7 @@ int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const doub
             R.wf[a] = float(R.w[a]);
             nc_tot *= R.nc[a];
         }
-        R.kz = p->cell_block > 0 ? std::min(p->cell_block, R.nc[2]) : 0;   // 0: chosen in md_create
+        R.kz = p->cell_block > 0 ? pow2_floor(std::min(p->cell_block, R.nc[2])) : 0;   // 0: chosen in md_create
         R.n = int32_t(n_rep[r]);
         R.slot0 = slot;
         R.tile0 = int32_t(slot / TILE);
@@ -628,14 +636,15 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     cudaError_t e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) { delete s; return fail(MD_ERR_CUDA, cudaGetErrorString(e)); }
     s->nsm = prop.multiProcessorCount;
-    // blocks of the cell order: about sqrt(rows of cells per SM's slot range) planes, at most 8
-    // (measured on the 4M-atom WCA fluid: 4 and 8 equally fast, 12 slower, 1 slowest)
+    // blocks of the cell order: about sqrt(rows of cells per SM's slot range) planes, rounded down
+    // to a power of two, at most 8 (measured on the 4M-atom WCA fluid: 4 and 8 equally fast, 12
+    // slower, 1 slowest)
     for (Rep& R : s->plan.reps) {
         if (R.kz > 0) continue;
         const double rows = double(R.nc[1]) * double(R.nc[2]);
         const double per_range = double(s->plan.nslots) / double(std::max(1, s->nsm)) * rows / double(R.n);
         const int kz = int(std::lround(std::sqrt(per_range)));
-        R.kz = std::max(1, std::min(std::min(kz, 8), int(R.nc[2])));
+        R.kz = pow2_floor(std::max(1, std::min(std::min(kz, 8), int(R.nc[2]))));
     }
     s->smem_per_sm = int(prop.sharedMemPerMultiprocessor);
     s->smem_per_cta = int(prop.sharedMemPerBlockOptin);
