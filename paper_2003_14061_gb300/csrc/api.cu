@@ -648,7 +648,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     }
     s->smem_per_sm = int(prop.sharedMemPerMultiprocessor);
     s->smem_per_cta = int(prop.sharedMemPerBlockOptin);
-    s->tune.ctas_per_sm = 12;
+    s->tune.ctas_per_sm = 8;            // the measured best for the 4M-atom fluid (the tuner searches 4-16)
     s->tune.nbr_batch = 2;
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
