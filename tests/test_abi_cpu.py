@@ -84,3 +84,33 @@ def test_slot_and_cell_limits():
     p = make_params(n=(1 << 26) + 1, box=(460.0, 460.0, 460.0), skin=0.0)
     assert B.lib().md_workspace_bytes(ctypes.byref(p)) == 0
     assert "2^26" in B.last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of md_params, md_props and md_tuning against the header, compiled as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"md_params": B.md_params, "md_props": B.md_props, "md_tuning": B.md_tuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gbmd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            *key, val = ln.split()
+            got[tuple(key)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
