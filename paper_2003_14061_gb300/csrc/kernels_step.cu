@@ -112,16 +112,22 @@ __device__ __forceinline__ AccF pair_loop_f32(const Scal& S, const Rep& R, float
     return AccF{-(fx.x + fx.y), -(fy.x + fy.y), -(fz.x + fz.y), u.x + u.y, w.x + w.y};
 }
 
-// the pair loop with W read from global memory
+// the pair loop with W read from global memory, over the first mm rows of the atom's column
 template <int NB>
-__device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const Rep& R,
-                                          const float4* __restrict__ pos, int64_t slot, float4 pi)
+__device__ __forceinline__ AccF force_f32_rows(const Arrays& A, const Scal& S, const Rep& R,
+                                               const float4* __restrict__ pos, int64_t slot, float4 pi, int mm)
 {
-    const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
     const uint32_t* __restrict__ Wc = A.W + slot;
     const int64_t ns = S.nslots;
     return pair_loop_f32<NB>(S, R, pi, mm, [=](int m) { return __ldcs(Wc + int64_t(m) * ns); },
                              [=](uint32_t e) { return __ldg(pos + (e >> IDX_SHIFT)); });
+}
+
+template <int NB>
+__device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const Rep& R,
+                                          const float4* __restrict__ pos, int64_t slot, float4 pi)
+{
+    return force_f32_rows<NB>(A, S, R, pos, slot, pi, min(__ldcs(A.nbr_count + slot), S.cap));
 }
 
 // Leapfrog kick and drift of one atom (Sec. 4.3 item 1) from its force a: MD_MIXED advances the
@@ -670,6 +676,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
     // L2 and the claim of the one after it is in flight
     int w0 = claim_now();
     int w1 = (w0 >= 0) ? claim_now() : -1;
+    int c0 = (w0 >= 0) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
     int run_r = -1, run_cnt = 0;
     float run_max = 0.0f;
     while (w0 >= 0) {
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         for (int q = 0; q < NPROP; ++q) part[q] = 0.0;
         if (active) {
             const float4 pi = __ldg(pos + slot);
-            const AccF a = force_f32<NB>(A, S, R, pos, slot, pi);
+            const AccF a = force_f32_rows<NB>(A, S, R, pos, slot, pi, min(c0, S.cap));
             double v[3], x[3];
             float v32[3], pn[3];
 #pragma unroll
@@ -786,6 +793,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         }
         w0 = w1;
         w1 = w2;
+        c0 = c1;                                 // read one warp-tile ahead
     }
     if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond);
     // the last warp of the launch resets the counters; the next launch is ordered after this one
