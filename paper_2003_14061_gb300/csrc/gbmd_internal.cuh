@@ -14,7 +14,8 @@
 //     consecutive atoms are adjacent, so the per-atom loop reads it coalesced).  An entry holds
 //     (o_x+1) | (o_y+1) << 2 | (o_z+1) << 4 in bits 0..5 and the neighbour slot in bits 6..31,
 //     o being the periodic offset of the neighbour's cell relative to the atom's cell.
-//   * Cells are numbered globally: replica r's cells are cell0_r + (c_z n_y + c_y) n_x + c_x.
+//   * Cells are numbered globally: replica r's cells are cell0_r + row_pos(c_y, c_z) n_x + c_x,
+//     the rows of cells in blocks of kz planes (row_pos below).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -181,21 +182,25 @@ __device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz)
 // so that a contiguous range of cells (and of slots, after a reorder) is compact along all three
 // axes; kz = 1 is the plain (z, y) row order.  kz is a power of two, so the block of a plane is a
 // shift (the build looks up 9 rows per atom).
-__device__ __forceinline__ int row_pos(const Rep& R, int ny, int nz)
+__host__ __device__ __forceinline__ int row_pos(const Rep& R, int ny, int nz)
 {
+#ifdef __CUDA_ARCH__
     const int sh = __ffs(R.kz) - 1;
+#else
+    const int sh = __builtin_ffs(R.kz) - 1;
+#endif
     const int z0 = (nz >> sh) << sh;
     const int hb = min(R.kz, R.nc[2] - z0);
     return z0 * R.nc[1] + ny * hb + (nz - z0);
 }
 
-__device__ __forceinline__ int cell_index(const Rep& R, int cx, int cy, int cz)
+__host__ __device__ __forceinline__ int cell_index(const Rep& R, int cx, int cy, int cz)
 {
     return R.cell0 + row_pos(R, cy, cz) * R.nc[0] + cx;
 }
 
 // (cx, cy, cz) of the replica-local cell number cl
-__device__ __forceinline__ void cell_coords(const Rep& R, int cl, int& cx, int& cy, int& cz)
+__host__ __device__ __forceinline__ void cell_coords(const Rep& R, int cl, int& cx, int& cy, int& cz)
 {
     cx = cl % R.nc[0];
     const int p = cl / R.nc[0];
