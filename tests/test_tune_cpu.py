@@ -1,0 +1,74 @@
+"""The autotuner's search and cache, on the CPU with a stand-in system whose step time is a known
+function of the launch shape (the GPU test times real steps)."""
+import json
+
+import pytest
+
+from paper_2003_14061_gb300 import binding as B
+from paper_2003_14061_gb300 import tune
+
+
+class FakeParams:
+    def __init__(self, precision):
+        self.precision = precision
+
+
+class FakeSystem:
+    def __init__(self, precision=B.MD_MIXED):
+        self.params = FakeParams(precision)
+        self.t = {"ctas_per_sm": 8, "nbr_batch": 2, "build_batch": 2, "use_graph": 1, "step_kernel": 1}
+        self.set_calls = []
+        self.steps = 0
+
+    def tuning(self):
+        return dict(self.t)
+
+    def set_tuning(self, **kw):
+        self.set_calls.append(dict(kw))
+        self.t.update({k: v for k, v in kw.items() if v})
+
+    def integrate(self, n):
+        self.steps += n
+
+
+def cost(t):
+    # a unique minimum at step kernel 1, 12 CTAs/SM, 4 entries per batch, build batch 4
+    c = 1.0 + 0.1 * abs(t["ctas_per_sm"] - 12) + 0.05 * abs(t["nbr_batch"] - 4)
+    c += {1: 0.0, 2: 0.5, 3: 0.7}[t["step_kernel"]] + {2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
+    return c
+
+
+@pytest.fixture
+def fake_timing(monkeypatch):
+    monkeypatch.setattr(tune, "_time_steps", lambda system, steps: cost(system.tuning()))
+    monkeypatch.setattr(tune, "signature", lambda system: f"fake|prec{system.params.precision}")
+
+
+def test_search_finds_the_fastest_shape(fake_timing):
+    s = FakeSystem()
+    res = tune.tune(s, steps=64)
+    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1}
+    assert res["ms_per_step"] == pytest.approx(1.0)
+    assert res["ms_per_step"] == min(res["trials"].values())
+    tried = [json.loads(k) for k in res["trials"]]
+    assert {t["step_kernel"] for t in tried} == {1, 2, 3}
+    assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 1} == set(tune.CTAS)
+    assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 2} == set(tune.CTAS_RING)
+    assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 3} == set(tune.CTAS_STAGED)
+    assert s.tuning()["ctas_per_sm"] == 12 and s.tuning()["build_batch"] == 4
+    assert s.steps % 16 == 0                       # whole 16-step graph replays only
+
+
+def test_fp64_searches_the_per_thread_kernel_only(fake_timing):
+    res = tune.tune(FakeSystem(B.MD_FP64), steps=32)
+    assert {json.loads(k)["step_kernel"] for k in res["trials"]} == {1}
+
+
+def test_cache_round_trip(fake_timing, tmp_path):
+    cache = str(tmp_path / "sub" / "tune.json")
+    first = tune.tune(FakeSystem(), steps=32, cache=cache)
+    s = FakeSystem()
+    again = tune.tune(s, steps=32, cache=cache)
+    assert again["best"] == first["best"]
+    assert s.steps == 0                            # served from the cache: nothing timed
+    assert s.set_calls == [first["best"]]
