@@ -9,7 +9,12 @@ Pins used (none re-types the oracle's formula):
   * invariants: zero net force, sum u_i = 2U, momentum conservation, bounded energy drift,
     time reversibility, second-order convergence against a tight ODE integration;
   * neighbour sets against the brute-force distance definition;
-  * the paper's printed neighbour statistics (tests/golden/paper_statistics.json);
+  * the paper's printed neighbour statistics and refresh intervals
+    (tests/golden/paper_statistics.json);
+  * hand-computed rebuild steps of both refresh rules for atoms at constant velocity;
+  * the sampled checkers used at full size (forces on listed atoms, neighbour sets of listed
+    atoms) against the whole-system evaluations pinned above;
+  * the pressure with a non-zero virial and the trajectory loss, written out from pinned pieces;
   * finite differences for the Jacobian, the parameter derivatives and the adjoint.
 """
 import json
@@ -169,6 +174,29 @@ def test_props_ideal_lattice():
     assert vmax == pytest.approx(np.sqrt((v ** 2).sum(1)).max(), rel=1e-15)
 
 
+@pytest.mark.parametrize("pot_name,r", [("wca", 1.0), ("lj", 1.5), ("lj", 1.05)])
+def test_pressure_with_virial(pot_name, r):
+    # one interacting pair at distance r across the periodic boundary: W = r . f(r) =
+    # 24 (2 r^-12 - r^-6) (repulsive: W > 0; LJ at r = 1.5 attractive: W < 0), U = u(r), and the
+    # pressure is (2K + W) / (3V) with K from the given velocities
+    L = 7.0
+    box = np.array([L, L, L])
+    x = np.array([[0.5 * r, 3.0, 3.5], [L - 0.5 * r, 3.0, 3.5]])
+    v = np.array([[0.3, -0.2, 0.7], [-0.1, 0.4, -0.5]])
+    p = wca() if pot_name == "wca" else lj()
+    W_want = 24.0 * (2.0 * r ** -12 - r ** -6)
+    u_lj = 4.0 * (r ** -12 - r ** -6)
+    U_want = u_lj + 1.0 if pot_name == "wca" else u_lj - 4.0 * (2.5 ** -12 - 2.5 ** -6)
+    K = 0.5 * float((v ** 2).sum())
+    U, Kp, W, P, px, py, pz, vmax = oracle.props(x, v, box, p)
+    assert W == pytest.approx(W_want, rel=1e-13)
+    assert U == pytest.approx(U_want, rel=1e-13, abs=1e-15)
+    assert Kp == pytest.approx(K, rel=1e-15)
+    assert P == pytest.approx((2.0 * K + W_want) / (3.0 * L ** 3), rel=1e-13)
+    assert [px, py, pz] == pytest.approx([0.2, 0.2, 0.2], abs=1e-15)
+    assert W != 0.0
+
+
 # ---------------------------------------------------------------------------------------------
 # integrator
 # ---------------------------------------------------------------------------------------------
@@ -235,6 +263,28 @@ def test_kdk_second_order_against_ode():
     assert 3.0 < errs[0] / errs[1] < 5.0        # second order: halving dt quarters the error
 
 
+@pytest.mark.parametrize("rule", [1, 2])
+@pytest.mark.parametrize("start", [2.0, 19.5])
+def test_refresh_rules_hand_count(rule, start):
+    # Three atoms that never come within r_c of each other; only atom 0 moves, at constant
+    # speed u along x (from x = 19.5 it crosses the periodic boundary at x = 20).  After n steps
+    # it has moved n dt u, and both rules fire at the first step with n dt u > skin/2:
+    # 0.3 / (0.005 * 1.7) = 35.29, so at steps 36, 72, 108, 144 and 180 -- five rebuilds in 200
+    # steps, four in 179, one in 71, none in 35.
+    L = 20.0
+    box = np.array([L, L, L])
+    x = np.array([[start, 5.0, 5.0], [10.0, 12.0, 10.0], [15.0, 2.0, 14.0]])
+    v = np.array([[1.7, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    for nsteps, want in ((35, 0), (36, 1), (71, 1), (179, 4), (200, 5)):
+        x1, v1, _, rb = oracle.run(x, v, box, wca(), dt=0.005, nsteps=nsteps, rule=rule, skin=0.6,
+                                   with_props=False)
+        assert rb == want, (nsteps, rb)
+        assert np.array_equal(v1, v)                                   # no force acted
+        assert x1[0, 0] == pytest.approx((start + nsteps * 0.005 * 1.7) % L, abs=1e-12)
+    # rule 0 counts nothing
+    assert oracle.run(x, v, box, wca(), dt=0.005, nsteps=200, rule=0, skin=0.6, with_props=False)[3] == 0
+
+
 # ---------------------------------------------------------------------------------------------
 # cells and neighbour sets
 # ---------------------------------------------------------------------------------------------
@@ -280,6 +330,52 @@ def test_neighbour_sets_match_definition(fp32):
     assert np.array_equal(counts, got.sum(1))
 
 
+@pytest.mark.parametrize("fp32", [True, False])
+def test_neighbours_sample_matches_full_sets(fp32):
+    # the sampled neighbour checker (used on the full-size workloads) returns, for each listed
+    # atom, the full count and the same ascending set as the whole-system evaluation pinned
+    # above; with a capacity below the count it keeps `cap` members of that set, ascending
+    x, box = inputs.fcc_lattice(5, 0.8)
+    x = inputs.perturb(x, box, 0.25, seed=21)
+    rc, skin = RC_WCA, 0.4
+    _, counts, off, nb = oracle.neighbours(x, box, rc, skin, fp32=fp32)
+    n = x.shape[0]
+    sample = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(3).choice(n, 80, replace=False)]))
+    cap = int(counts.max())
+    sc, snb = oracle.neighbours_sample(x, box, rc, skin, sample, cap, fp32=fp32)
+    assert np.array_equal(sc, counts[sample])
+    for k, i in enumerate(sample):
+        assert np.array_equal(snb[k, : sc[k]], nb[off[i]: off[i + 1]])
+        assert np.all(snb[k, sc[k]:] == -1)
+    capt = int(np.median(counts)) - 2
+    assert (counts[sample] > capt).any()
+    tc, tnb = oracle.neighbours_sample(x, box, rc, skin, sample, capt, fp32=fp32)
+    assert np.array_equal(tc, counts[sample])                      # the full count is reported
+    for k, i in enumerate(sample):
+        row = tnb[k, : min(capt, tc[k])]
+        assert np.all(np.diff(row) > 0)
+        assert np.isin(row, nb[off[i]: off[i + 1]]).all()
+        if tc[k] <= capt:
+            assert np.array_equal(row, nb[off[i]: off[i + 1]])
+
+
+@pytest.mark.parametrize("pot_name", ["wca", "lj"])
+def test_force_on_atoms_matches_whole_system(pot_name):
+    # the sampled force checker (used on the full-size workloads) equals the whole-system
+    # evaluation, itself pinned to brute force above, on every listed atom
+    rho = 0.8 if pot_name == "wca" else 0.8442
+    x, box = inputs.fcc_lattice(5, rho)
+    x = inputs.perturb(x, box, 0.12, seed=13)
+    p = wca() if pot_name == "wca" else lj()
+    f, ua, _, _ = oracle.forces(x, box, p)
+    n = x.shape[0]
+    sample = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(4).choice(n, 60, replace=False)]))
+    fs, us = oracle.force_on_atoms(x, box, p, sample)
+    assert np.abs(f[sample]).max() > 1.0
+    assert np.abs(fs - f[sample]).max() <= 1e-14 * np.abs(f).max()
+    assert np.abs(us - ua[sample]).max() <= 1e-14 * (np.abs(ua).max() + 1.0)
+
+
 def test_neighbour_count_perfect_fcc():
     # rho = 0.8: first shell 12 at 1.2091, second 6 at 1.7100 > r_c + 0.4 = 1.5225
     x, box = inputs.fcc_lattice(6, 0.8)
@@ -299,15 +395,50 @@ def _equilibrate(x, v, box, p, T, nsteps, chunk=100):
     return x, v
 
 
+_EQUILIBRATED = {}
+
+
+def _paper_state(name):
+    """The paper's SP or LJ state (Sec. 3.1), 1372 atoms equilibrated at its temperature."""
+    if name not in _EQUILIBRATED:
+        ref = json.load(open(os.path.join(GOLDEN, "paper_statistics.json")))[name]
+        x, box = inputs.fcc_lattice(7, ref["rho"])
+        v = inputs.maxwell(x.shape[0], ref["T"], seed=7)
+        p = oracle.pot(rc=ref["rc"], shift=True)
+        x, v = _equilibrate(x, v, box, p, ref["T"], 1500)
+        _EQUILIBRATED[name] = (ref, x, v, box, p)
+    return _EQUILIBRATED[name]
+
+
 @pytest.mark.parametrize("name", ["SP", "LJ"])
 def test_paper_mean_neighbour_counts(name):
-    ref = json.load(open(os.path.join(GOLDEN, "paper_statistics.json")))[name]
-    x, box = inputs.fcc_lattice(7, ref["rho"])
-    v = inputs.maxwell(x.shape[0], ref["T"], seed=7)
-    p = oracle.pot(rc=ref["rc"], shift=True)
-    x, v = _equilibrate(x, v, box, p, ref["T"], 1500)
+    ref, x, v, box, p = _paper_state(name)
     nc, counts, off, nb = oracle.neighbours(x, box, ref["rc"], ref["skin"], fp32=False)
     assert counts.mean() == pytest.approx(ref["mean_neighbours"], rel=0.10)
+
+
+@pytest.mark.parametrize("name,tiles,nsteps", [("SP", 6, 60), ("LJ", 5, 60)])
+def test_paper_refresh_interval(name, tiles, nsteps):
+    # Sec. 4.1 item 5: the largest systems refresh every 10.2 (SP) and 9.8 (LJ) steps at
+    # delta = 0.6 under the maximum-velocity rule.  That interval is about (delta/2) / (dt vmax),
+    # and vmax, the largest speed among N atoms, grows with N (the extreme of N Maxwell draws),
+    # so a 1372-atom state refreshes every ~14 steps.  The state here has the size the interval
+    # needs: the equilibrated 1372-atom configuration repeated tiles^3 times (a periodic
+    # configuration of the larger box; 296k and 171k atoms) with fresh Maxwell velocities at the
+    # state's temperature -- in equilibrium positions and momenta are independent, so this is an
+    # equilibrium state of the larger system.  vmax is still below that of the paper's 16.8M
+    # (SP) and 7.1M (LJ) atoms, which biases the interval up by a few per cent.  The rule counts
+    # whole steps, so the count c over nsteps admits any interval in (nsteps/(c+1), nsteps/c];
+    # that range must meet the paper's figure +-15%.
+    ref, x, _, box, p = _paper_state(name)
+    sh = np.stack(np.meshgrid(*[np.arange(tiles)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    X = np.ascontiguousarray((x[None, :, :] + sh[:, None, :] * box[None, None, :]).reshape(-1, 3))
+    B = box * tiles
+    V = inputs.maxwell(X.shape[0], ref["T"], seed=8)
+    _, _, _, c = oracle.run(X, V, B, p, dt=0.005, nsteps=nsteps, rule=1, skin=ref["skin"], with_props=False)
+    lo, hi = nsteps / (c + 1), nsteps / max(c, 1e-9)
+    want = ref["refresh_steps"]
+    assert c > 0 and lo < 1.15 * want and hi >= 0.85 * want, (c, lo, hi, want)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -381,6 +512,27 @@ def test_adjoint_matches_finite_difference():
         vm = v.copy(); vm[i, a] -= h
         fd = (L(vv=vp) - L(vv=vm)) / (2 * h)
         assert gv[i, a] == pytest.approx(fd, rel=1e-5, abs=1e-7)
+
+
+def test_loss_closed_form():
+    # L = (1/S) sum_{n=1..S} U(x_n) + |v_S|^2, written out for S = 1 and 2 from the pinned force
+    # evaluation and the leapfrog steps: x_{n+1} = x_n + dt (v_n + c F_n), v_{n+1} = v_n + c (F_n
+    # + F_{n+1}), c = dt / 2m
+    x, box = _snapshot(seed=7, ncell=3, amp=0.12)
+    v = inputs.maxwell(x.shape[0], 1.0, seed=8)
+    dt = 0.005
+    c = dt / 2
+    f0, _, _, _ = oracle.forces(x, box, wca())
+    x1 = np.mod(x + dt * (v + c * f0), box)
+    f1, _, U1, _ = oracle.forces(x1, box, wca())
+    v1 = v + c * (f0 + f1)
+    x2 = np.mod(x1 + dt * (v1 + c * f1), box)
+    f2, _, U2, _ = oracle.forces(x2, box, wca())
+    v2 = v1 + c * (f1 + f2)
+    assert U1 > 1.0 and U2 > 1.0
+    assert oracle.loss(x, v, box, wca(), dt=dt, nsteps=1) == pytest.approx(U1 + (v1 ** 2).sum(), rel=1e-13)
+    assert oracle.loss(x, v, box, wca(), dt=dt, nsteps=2) == pytest.approx(0.5 * (U1 + U2) + (v2 ** 2).sum(),
+                                                                          rel=1e-13)
 
 
 def test_adjoint_single_step_closed_form():
