@@ -110,6 +110,7 @@ typedef struct {
     int64_t rebuilds;      /* neighbour-matrix rebuilds since creation or md_set_state */
     int32_t max_cell_occ;  /* N_l = max_c k_c at the last rebuild (Sec. 2.3 step N3) */
     int32_t max_nbrs;      /* max_i m_i at the last rebuild */
+    int64_t reorders;      /* reorders by cell since creation or md_set_state (both reorder) */
 } md_props;
 
 /* Size of the workspace for one system (md_create) or a batch (md_create_batch); 0 on error. */
@@ -118,8 +119,9 @@ size_t md_workspace_bytes_batch(const md_params* p, int32_t nrep, const int64_t*
                                 const double* box_rep);
 
 /* Create one system of p->n atoms in box p->box.  x0, v0: host or device, [n][3] FP64 in id
- * order; positions are wrapped into the box.  The call bins the atoms, reorders them by cell and
- * builds the neighbour matrix (N1-N5).  stream: cudaStream_t (NULL = legacy default stream). */
+ * order; positions are wrapped into the box (any number of box lengths away).  The call bins the
+ * atoms, reorders them by cell and builds the neighbour matrix (N1-N5).  A non-finite x0 or v0
+ * component fails with MD_ERR_NONFINITE.  stream: cudaStream_t (NULL = legacy default stream). */
 int md_create(const md_params* p, void* d_workspace, size_t workspace_bytes, const double* x0,
               const double* v0, void* stream, md_system** out);
 
@@ -174,7 +176,9 @@ int md_props_latest(md_system* s, double* dst);
 int md_get_state(md_system* s, double* x, double* v, double* f);
 
 /* Replace positions and velocities (id order, [n_total][3] FP64, host or device), resetting the
- * step and rebuild counters, then bin, reorder and rebuild W as md_create does. */
+ * step and rebuild counters, then bin, reorder and rebuild W as md_create does.  A non-finite
+ * component fails with MD_ERR_NONFINITE (the state is then unusable until the next successful
+ * md_set_state). */
 int md_set_state(md_system* s, const double* x, const double* v);
 
 /* Diagnostics in id order (host pointers), from the last binning / rebuild:
@@ -184,8 +188,17 @@ int md_set_state(md_system* s, const double* x, const double* v);
 int md_get_cells(md_system* s, int32_t* cell);
 int md_get_neighbours(md_system* s, int32_t* counts, int32_t* nbr_ids, int32_t cap);
 
-/* Waits for the stream and returns the first latched device error (then clears it). */
+/* Waits for the stream and returns the first latched device error (then clears it).  A
+ * non-finite value is reported before a neighbour overflow it may have caused. */
 int md_check(md_system* s);
+
+/* Test hook for the error-reporting path (the paper has no counterpart): queues, on the system's
+ * stream, a one-thread kernel that sets the device error word as a kernel meeting the condition
+ * would.  status: MD_ERR_NBR_OVERFLOW, MD_ERR_NONFINITE or MD_ERR_TIMEOUT (else
+ * MD_ERR_INVALID_ARG).  The next call that waits (md_check, md_reduce_props, ...) returns that
+ * status and clears it, so conditions a healthy run never meets -- a bounded device wait giving
+ * up -- can be tested without making any kernel fail. */
+int md_debug_set_error(md_system* s, int32_t status);
 
 /* Sizes: replicas, total atoms, rows of W, cells per axis of replica r (nc[3]). */
 int32_t md_nrep(const md_system* s);
@@ -267,22 +280,28 @@ int md_get_timing(md_system* s, double* ms, int64_t* calls, int64_t* launches);
 int md_destroy(md_system* s);
 
 /* Forces for a small system without any device allocation (the paper has no counterpart).
- * For callers that cannot allocate device memory where they need forces -- code issuing work
- * while a stream is being captured into a CUDA graph, hosts that only hand out pre-planned
- * buffers, loops that must not risk the synchronisation of cudaMalloc/cudaFree -- this computes
- * f_i and u_i as md_compute_forces does (FP32 pair arithmetic on cell-local coordinates), over a
- * plain cell list of side >= rc (skin is ignored) kept in one file-scope device array of
- * 1.75 MiB that every GPU loading the library holds until exit.
+ * For callers that cannot allocate device memory where they need forces -- code inside another
+ * runtime or framework that owns the device allocator and hands out only pre-planned buffers,
+ * plug-ins running between someone else's kernels where the synchronisation of cudaMalloc/
+ * cudaFree is not allowed, code with no workspace to hand -- this computes f_i and u_i as
+ * md_compute_forces does (FP32 pair arithmetic on cell-local coordinates), over a plain cell
+ * list of side >= rc (skin is ignored) kept in one file-scope device array of 1.75 MiB that
+ * every GPU loading the library holds until exit.  The atoms of each cell are visited in index
+ * order, so repeated calls on the same input return the same bits.
  *   p      : eps, sigma, rc, shift_energy and box are used; the rest is ignored.
  *   n      : 1..65536 atoms; the box may hold at most 65536 cells of side >= rc
  *            (MD_ERR_INVALID_ARG otherwise, before any work is queued; md_last_error says which).
- *   x      : device, [n][3] FP64 positions (wrapped into the box on the fly).
+ *   x      : device, [n][3] FP64 positions, any number of box lengths from the box (wrapped
+ *            into it on the fly).
  *   f      : device, [n][3] FP64 output forces;  u: device, [n] FP64 output u_i, or NULL.
  *   stream : cudaStream_t as void*; the call only queues work and does not wait.
  * The array is shared by all calls and keeps the last call's contents (each call clears what it
  * needs to start at zero); calls whose work overlaps on the GPU race on it and must not be
  * issued.  The first call on each device looks up the array's device address with that device
- * current, so it should come before any stream capture.  Calls no cudaMalloc or cudaFree. */
+ * current, so it should come before any stream capture; the address is kept until the process
+ * exits, so the call must not be used on a device after cudaDeviceReset.  A launch error left
+ * pending by earlier, unrelated work is cleared on entry rather than reported.  Calls no
+ * cudaMalloc or cudaFree. */
 int md_forces_static(const md_params* p, int64_t n, const double* x, double* f, double* u, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */

@@ -27,7 +27,7 @@ EXPORTS = (
     "md_clear_series", "md_get_state", "md_set_state", "md_get_cells", "md_get_neighbours", "md_check",
     "md_nrep", "md_natoms", "md_nbr_capacity", "md_cells_per_axis", "md_set_tuning", "md_get_tuning",
     "md_destroy", "md_last_error", "md_set_timing", "md_get_timing", "md_forces_static",
-    "md_adjoint_workspace_bytes", "md_adjoint", "md_props_latest",
+    "md_adjoint_workspace_bytes", "md_adjoint", "md_props_latest", "md_debug_set_error",
 )
 NPHASE = 6
 PHASES = ("step", "bin", "reorder", "build", "props", "other")
@@ -53,7 +53,8 @@ class md_props(ctypes.Structure):
     _fields_ = [("U", ctypes.c_double), ("K", ctypes.c_double), ("E_per_atom", ctypes.c_double),
                 ("virial", ctypes.c_double), ("pressure", ctypes.c_double), ("P", ctypes.c_double * 3),
                 ("vmax", ctypes.c_double), ("mean_nbrs", ctypes.c_double), ("step", ctypes.c_int64),
-                ("rebuilds", ctypes.c_int64), ("max_cell_occ", ctypes.c_int32), ("max_nbrs", ctypes.c_int32)]
+                ("rebuilds", ctypes.c_int64), ("max_cell_occ", ctypes.c_int32), ("max_nbrs", ctypes.c_int32),
+                ("reorders", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +120,7 @@ def lib(build_if_missing: bool = True):
             "md_adjoint_workspace_bytes": (sz, [vp, i32, i32]),
             "md_adjoint": (ctypes.c_int, [vp, vp, sz, i32, i32, vp, vp, vp, vp]),
             "md_props_latest": (ctypes.c_int, [vp, vp]),
+            "md_debug_set_error": (ctypes.c_int, [vp, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -427,10 +427,12 @@ int latch_error(md_system* s)
     const int zero = 0;
     GBMD_CUDA(cudaMemcpyAsync(&s->A.g->err, &zero, sizeof(int), cudaMemcpyHostToDevice, s->L.stream));
     GBMD_CUDA(cudaStreamSynchronize(s->L.stream));
+    // a non-finite input or state is the root cause of anything else it triggers (a NaN position
+    // binned to cell 0 can overflow that cell's neighbours), so it is reported first
+    if (g.err & ERR_NONFINITE) return fail(MD_ERR_NONFINITE, "non-finite position, velocity or displacement");
     if (g.err & ERR_NBR_OVERFLOW)
         return fail(MD_ERR_NBR_OVERFLOW, "neighbour capacity " + std::to_string(s->plan.cap) +
                                              " exceeded (an atom had " + std::to_string(g.max_nbr_seen) + ")");
-    if (g.err & ERR_NONFINITE) return fail(MD_ERR_NONFINITE, "non-finite velocity or displacement");
     if (g.err & ERR_TIMEOUT) return fail(MD_ERR_TIMEOUT, "a bounded device wait gave up");
     return fail(MD_ERR_CUDA, "unknown device error word");
 }
@@ -926,6 +928,18 @@ int md_check(md_system* s)
     if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
     GBMD_CUDA(cudaGetLastError());
     return latch_error(s);
+}
+
+int md_debug_set_error(md_system* s, int32_t status)
+{
+    if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
+    int bits = 0;
+    if (status == MD_ERR_NBR_OVERFLOW) bits = ERR_NBR_OVERFLOW;
+    else if (status == MD_ERR_NONFINITE) bits = ERR_NONFINITE;
+    else if (status == MD_ERR_TIMEOUT) bits = ERR_TIMEOUT;
+    else return fail(MD_ERR_INVALID_ARG, "status must be MD_ERR_NBR_OVERFLOW, MD_ERR_NONFINITE or MD_ERR_TIMEOUT");
+    GBMD_CUDA(launch_debug_error(s->A, s->L, bits, s->plan.cap + 1));
+    return MD_OK;
 }
 
 int32_t md_nrep(const md_system* s) { return s ? s->plan.nrep : 0; }

@@ -70,6 +70,7 @@ struct RepState {             // per replica, mutable on the device
     int64_t rebuilds;
     int64_t last_reorder;     // step of the last reorder
     int64_t sum_nbrs;         // sum m_i at the last rebuild
+    int64_t reorders;         // reorders since creation or md_set_state
 };
 
 struct Global {               // device-wide words
@@ -424,6 +425,10 @@ struct Launch {
 
 // records msg for md_last_error() on this thread and returns code (api.cu)
 int set_last_error(int code, const char* msg);
+
+// md_debug_set_error: ORs ErrBits into the device error word as a kernel meeting the condition
+// would (kernels_step.cu)
+cudaError_t launch_debug_error(const Arrays& A, const Launch& L, int bits, int nbr_seen);
 
 // rebuild path (kernels_rebuild.cu)
 cudaError_t launch_force_rebuild(const Arrays& A, const Scal& S, const Launch& L, int reorder);

@@ -135,8 +135,17 @@ __global__ void __launch_bounds__(TILE) k_bin(Arrays A, Scal S, int cur, int fro
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 double xa = x[a];
+                if (!isfinite(xa)) {                  // reported; the atom goes to cell 0
+                    atomicOr(&A.g->err, ERR_NONFINITE);
+                    xa = 0.0;
+                }
                 if (xa < 0.0) xa = __dadd_rn(xa, R.L[a]);
                 if (xa >= R.L[a]) xa = __dsub_rn(xa, R.L[a]);
+                if (!(xa >= 0.0 && xa < R.L[a])) {    // more than one period away: whole periods
+                    xa = __dsub_rn(xa, __dmul_rn(R.L[a], floor(xa / R.L[a])));
+                    if (xa < 0.0) xa = __dadd_rn(xa, R.L[a]);
+                    if (xa >= R.L[a]) xa = __dsub_rn(xa, R.L[a]);
+                }
                 int ca = int(floor(__dmul_rn(xa, R.s[a])));
                 ca = min(max(ca, 0), R.nc[a] - 1);
                 c[a] = ca;
@@ -1007,7 +1016,10 @@ __global__ void k_rebuild_finish(Arrays A, Scal S, int in_graph)
     for (int r = threadIdx.x; r < S.nrep; r += blockDim.x) {
         RepState& st = A.rs[r];
         if (!st.rebuild) continue;
-        if (st.reorder) st.last_reorder = st.step;
+        if (st.reorder) {
+            st.last_reorder = st.step;
+            st.reorders += 1;
+        }
         st.reorder = 0;
         st.rebuild = 0;
         st.D = 0.0;

@@ -1089,6 +1089,7 @@ __global__ void __launch_bounds__(32) k_props_finalize(Arrays A, Scal S, int to_
     pr.rebuilds = st.rebuilds;
     pr.max_cell_occ = st.max_occ;
     pr.max_nbrs = st.max_nbrs;
+    pr.reorders = st.reorders;
     A.props[r] = pr;
     if (to_series) {
         RepState& sw = A.rs[r];
@@ -1117,14 +1118,18 @@ __global__ void __launch_bounds__(TILE) k_set_state(Arrays A, Scal S, int cur)
             RepState& st = A.rs[r];
             st.D = 0.0; st.vmax2 = 0u; st.rebuild = 0; st.reorder = 0; st.vhalf = 0;
             st.tiles_done = 0; st.max_nbrs = 0; st.max_occ = 0; st.series_rows = 0;
-            st.step = 0; st.rebuilds = 0; st.last_reorder = 0; st.sum_nbrs = 0;
+            st.step = 0; st.rebuilds = 0; st.last_reorder = 0; st.sum_nbrs = 0; st.reorders = 0;
         }
         if (j >= R.n) continue;
         const int64_t id = R.id0 + j;
         A.id[slot] = int32_t(id);
         for (int a = 0; a < 3; ++a) {
             A.xl[a][slot] = A.xchg[0][id * 3 + a];     // global position, origin cell (0,0,0)
-            const double v = A.xchg[1][id * 3 + a];
+            double v = A.xchg[1][id * 3 + a];
+            if (!isfinite(v)) {                        // reported by the call; the atom is held still
+                atomicOr(&A.g->err, ERR_NONFINITE);
+                v = 0.0;
+            }
             if (MODE == MD_FP32) A.v32[a][slot] = float(v);
             else A.v[a][slot] = v;
         }
@@ -1419,6 +1424,18 @@ cudaError_t launch_set_state(const Arrays& A, const Scal& S, const Launch& L, in
     if (S.mode == MD_FP64) k_set_state<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else if (S.mode == MD_MIXED) k_set_state<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else k_set_state<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    return cudaGetLastError();
+}
+
+__global__ void k_debug_error(Arrays A, int bits, int nbr_seen)
+{
+    atomicOr(&A.g->err, bits);
+    if (bits & ERR_NBR_OVERFLOW) atomicMax(&A.g->max_nbr_seen, nbr_seen);
+}
+
+cudaError_t launch_debug_error(const Arrays& A, const Launch& L, int bits, int nbr_seen)
+{
+    k_debug_error<<<1, 1, 0, L.stream>>>(A, bits, nbr_seen);
     return cudaGetLastError();
 }
 

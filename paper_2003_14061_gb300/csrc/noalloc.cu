@@ -1,13 +1,15 @@
 // noalloc.cu -- md_forces_static: pair forces for a small system without any device allocation.
 //
-// Some callers cannot allocate device memory at the point where they need forces: code running
-// while a stream is being captured into a CUDA graph (cudaMalloc is not capturable), host code
-// inside another runtime that hands out only pre-planned buffers, or latency-critical loops that
-// must not take the device-wide synchronisation a cudaMalloc/cudaFree can imply.  For them this
-// entry point keeps its cell-list scratch (occupancy counts, prefix sums, cell order, cell-local
-// positions) in one file-scope __device__ array of fixed size, instead of a caller-provided
-// workspace.  The computation is the force pass of md_compute_forces on a plain cell list of side
-// >= r_c (no neighbour matrix): FP32 pair arithmetic on cell-local coordinates, per-atom sums.
+// Some callers cannot allocate device memory at the point where they need forces: host code
+// inside another runtime or framework that hands out only pre-planned buffers and owns the
+// device allocator, plug-ins that run between someone else's kernels where a cudaMalloc/cudaFree
+// would take the device-wide synchronisation these calls can imply, or code that has no
+// workspace to hand.  For them this entry point keeps its cell-list scratch (occupancy counts,
+// prefix sums, cell order, cell-local positions) in one file-scope __device__ array of fixed
+// size, instead of a caller-provided workspace.  The computation is the force pass of
+// md_compute_forces on a plain cell list of side >= r_c (no neighbour matrix): FP32 pair
+// arithmetic on cell-local coordinates, per-atom sums in a fixed order (the atoms of each cell
+// ascending), so repeated calls on the same input give the same bits.
 //
 // Limits and sharing:
 //   * at most NA_MAX_ATOMS atoms and NA_MAX_CELLS cells (both 65536); larger requests fail with
@@ -18,7 +20,8 @@
 //     without ordering between them) race on the array and must not be issued;
 //   * the host needs the array's device address: the first call on each device looks it up
 //     (cudaGetSymbolAddress) with that device current, so that first call should come before any
-//     stream capture.
+//     stream capture; the address is kept for the life of the process, so the entry point must
+//     not be used after cudaDeviceReset on that device.
 #include <mutex>
 #include <string>
 
@@ -77,6 +80,11 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_bin(NaView V, NaGeom G, const
         double xa = x[3 * i + a];
         if (xa < 0.0) xa += G.L[a];
         if (xa >= G.L[a]) xa -= G.L[a];
+        if (!(xa >= 0.0 && xa < G.L[a])) {           // more than one period away: whole periods
+            xa -= G.L[a] * floor(xa / G.L[a]);
+            if (xa < 0.0) xa += G.L[a];
+            if (xa >= G.L[a]) xa -= G.L[a];
+        }
         int ca = int(floor(xa * G.s[a]));
         ca = min(max(ca, 0), G.nc[a] - 1);
         c[a] = ca;
@@ -128,6 +136,24 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_scatter(NaView V, NaGeom G)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < G.n) V.perm[V.start[V.cell[i]] + V.layer[i]] = i;
+}
+
+// the atomic layer slots leave the order inside a cell to chance; sorting each cell's atoms by
+// index fixes the summation order of every force, so repeated calls give identical bits
+__global__ void __launch_bounds__(NA_THREADS) k_na_sort(NaView V, NaGeom G)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= G.ncells) return;
+    const int b = V.start[c], e = V.start[c + 1];
+    for (int k = b + 1; k < e; ++k) {                // insertion sort: cells hold a few atoms
+        const int key = V.perm[k];
+        int q = k - 1;
+        while (q >= b && V.perm[q] > key) {
+            V.perm[q + 1] = V.perm[q];
+            --q;
+        }
+        V.perm[q + 1] = key;
+    }
 }
 
 // F1 over the 27 cells around each atom; force on i is g (x_i - x_j)
@@ -240,12 +266,14 @@ int md_forces_static(const md_params* p, int64_t n, const double* x, double* f, 
     }
     const NaView V = view_of(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    (void)cudaGetLastError();        // an earlier, unrelated launch error is not this call's failure
     e = cudaMemsetAsync(V.count, 0, sizeof(int32_t) * size_t(G.ncells), st);
     if (e != cudaSuccess) return na_fail(MD_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     const int blocks = int((n + NA_THREADS - 1) / NA_THREADS);
     k_na_bin<<<blocks, NA_THREADS, 0, st>>>(V, G, x);
     k_na_scan<<<1, 1024, 0, st>>>(V, G);
     k_na_scatter<<<blocks, NA_THREADS, 0, st>>>(V, G);
+    k_na_sort<<<(G.ncells + NA_THREADS - 1) / NA_THREADS, NA_THREADS, 0, st>>>(V, G);
     k_na_forces<<<blocks, NA_THREADS, 0, st>>>(V, G, f, u);
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(MD_ERR_CUDA, cudaGetErrorString(e));

@@ -185,6 +185,11 @@ class MDSystem:
     def check(self):
         self._call("md_check")
 
+    def debug_set_error(self, status: str):
+        """Latch a device error as a failing kernel would (tests of the reporting path)."""
+        code = {v: k for k, v in B.STATUS.items()}[status]
+        self._call("md_debug_set_error", int(code))
+
     def adjoint(self, nsteps: int, ckpt_every: int = 20, dv0_out: torch.Tensor = None):
         """Loss L = (1/S) sum_{n=1..S} U(x_n) + |v_S|^2 and (dL/deps, dL/dsigma, dL/dv0).
 

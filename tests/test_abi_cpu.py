@@ -114,3 +114,26 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def _create_status(n, box, **kw):
+    """md_create's status for a system whose host-side plan fails (no device work is reached)."""
+    L = B.lib()
+    p = make_params(n=n, box=box, **kw)
+    x = np.zeros((n, 3))
+    v = np.zeros((n, 3))
+    h = ctypes.c_void_p()
+    fake_ws = ctypes.c_void_p(1 << 20)          # never touched: the plan is refused first
+    rc = L.md_create(ctypes.byref(p), fake_ws, 1 << 30, x.ctypes.data_as(ctypes.c_void_p),
+                     v.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(h))
+    return B.STATUS[rc], h.value
+
+
+def test_create_reports_box_and_cell_errors():
+    # 2 cells of side r_c + skin along an axis (L = 3.0 < 3 (2^(1/6) + 0.4))
+    assert _create_status(64, (3.0, 10.0, 10.0)) == ("MD_ERR_BOX_TOO_SMALL", None)
+    assert "fewer than 3 cells" in B.last_error()
+    # 1024 cells along x
+    assert _create_status(64, (1024 * 1.6, 10.0, 10.0)) == ("MD_ERR_CELL_OVERFLOW", None)
+    assert "1023" in B.last_error()
+    assert _create_status(64, (10.0, 10.0, 10.0), eps=float("nan")) == ("MD_ERR_INVALID_ARG", None)

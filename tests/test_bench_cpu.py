@@ -80,3 +80,28 @@ def test_code_hash_ignores_comments_only(tmp_path):
     c.write_text("__global__ void k(int* p) { p[0] = 2; }\n")
     assert bench.code_hash(str(a)) == bench.code_hash(str(b))
     assert bench.code_hash(str(a)) != bench.code_hash(str(c))
+
+
+class _FakeClocks:
+    """Stand-in for the NVML source: a clock that drops and a power-cap reason on some samples."""
+
+    def __init__(self):
+        self.k = 0
+
+    def sample(self):
+        self.k += 1
+        return (2070.0 if self.k % 3 else 1900.0), 2070.0, (0x4 if self.k % 5 == 0 else 0)
+
+
+def test_clock_sampler_has_samples_for_a_short_region():
+    import time
+    import bench
+    with bench.ClockSampler(0, period=0.001, source=_FakeClocks()) as clk:
+        time.sleep(0.02)
+    s = clk.summary()
+    assert s["samples"] >= 3 and s["source"] == "nvml"
+    assert s["sm_max_mhz"] == 2070.0 and s["sm_mhz"] in (1900.0, 2070.0)
+    assert s["reasons"] in ([], ["sw_power_cap"])
+    with bench.ClockSampler(0, period=0.001, source=_FakeClocks()) as clk:
+        pass                                    # an empty region still has the entry and exit samples
+    assert clk.summary()["samples"] >= 2

@@ -5,6 +5,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle
+from paper_2003_14061_gb300 import binding as B
 from paper_2003_14061_gb300 import inputs
 from paper_2003_14061_gb300.system import WCA_RC, MDSystem
 
@@ -103,3 +104,62 @@ def test_batch_with_one_atom_replica_and_ragged_tails():
         xo, vo, _, _ = oracle.run(xb, vb, bb, oracle.pot(), dt=0.005, nsteps=40, with_props=False)
         assert np.abs(min_image(xg[off:off + n] - xo, bb)).max() <= 1e-4
         off += n
+
+
+def test_positions_several_box_lengths_away():
+    # md_create wraps any number of periods: cells, forces and the returned positions are those
+    # of the in-box positions
+    x, box = inputs.fcc_lattice(6, 0.8)
+    x = inputs.perturb(x, box, 0.15, 31)
+    k = np.random.default_rng(32).integers(-4, 5, x.shape)
+    assert (np.abs(k) >= 2).any()
+    v = inputs.maxwell(x.shape[0], 1.0, 33)
+    s = MDSystem(x + k * box, v, box, rc=WCA_RC, skin=0.4)
+    xg, _, f = s.state(f=True)
+    assert np.abs(min_image(xg - x, box)).max() <= 1e-12
+    _, cell = oracle.cells(x, box, WCA_RC + 0.4)
+    assert np.array_equal(s.cells(), cell)
+    of, _, _, _ = oracle.forces(x, box, oracle.pot())
+    assert np.linalg.norm(f - of) <= 1e-5 * np.linalg.norm(of)
+
+
+@pytest.mark.parametrize("what,bad", [("x", np.nan), ("v", np.nan), ("x", np.inf), ("v", -np.inf)])
+def test_nonfinite_state_is_reported(what, bad):
+    x, box = inputs.fcc_lattice(5, 0.8)
+    x = inputs.perturb(x, box, 0.1, 34)
+    v = inputs.maxwell(x.shape[0], 1.0, 35)
+    xb, vb = x.copy(), v.copy()
+    (xb if what == "x" else vb)[17, 1] = bad
+    with pytest.raises(B.MDError) as e:
+        MDSystem(xb, vb, box, rc=WCA_RC, skin=0.4)
+    assert e.value.status == "MD_ERR_NONFINITE"
+    s = MDSystem(x, v, box, rc=WCA_RC, skin=0.4)
+    with pytest.raises(B.MDError) as e:
+        s.set_state(xb, vb)
+    assert e.value.status == "MD_ERR_NONFINITE"
+    s.set_state(x, v)                                   # a good state makes the system usable again
+    s.integrate(20)
+    xg, _, _ = s.state()
+    xo, _, _, _ = oracle.run(x, v, box, oracle.pot(), dt=0.005, nsteps=20, with_props=False)
+    assert np.abs(min_image(xg - xo, box)).max() <= 1e-4
+
+
+@pytest.mark.parametrize("status", ["MD_ERR_TIMEOUT", "MD_ERR_NONFINITE", "MD_ERR_NBR_OVERFLOW"])
+def test_latched_device_errors_are_reported_once(status):
+    # the device error word set from the host, as a kernel meeting the condition would: the next
+    # call that waits returns the status and clears it (no kernel is made to fail)
+    x, box = inputs.fcc_lattice(4, 0.8)
+    v = inputs.maxwell(x.shape[0], 1.0, 36)
+    s = MDSystem(x, v, box, rc=WCA_RC, skin=0.4)
+    s.integrate(5)
+    s.debug_set_error(status)
+    with pytest.raises(B.MDError) as e:
+        s.check()
+    assert e.value.status == status
+    s.check()                                           # reported once
+    s.debug_set_error(status)
+    with pytest.raises(B.MDError) as e:
+        s.props()
+    assert e.value.status == status
+    s.integrate(5)
+    assert s.props()[0]["step"] == 10
