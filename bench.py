@@ -103,28 +103,110 @@ def make_inputs(name, rank=0, ncell=0):
     return x, v, dict(box=box)
 
 
-class ClockSampler:
-    """nvidia-smi samples of the SM clock and throttle reasons while the timed region runs."""
+class NvmlClocks:
+    """Read-only NVML queries (libnvidia-ml through ctypes) of one GPU: SM clock, its maximum and
+    the active clock-event reason bits.  Nothing is set."""
 
+    def __init__(self, dev_index: int = 0):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        rc = -1
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(dev_index)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(self.h))
+        except Exception:
+            rc = -1
+        if rc != 0 and self.lib.nvmlDeviceGetHandleByIndex_v2(int(dev_index), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle for the device")
+        self._u = ctypes.c_uint()
+        self._r = ctypes.c_ulonglong()
+        self._getr = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        """(sm_mhz, sm_max_mhz, reason_bits)"""
+        ct = self.ct
+        self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(self._u))          # NVML_CLOCK_SM
+        sm = float(self._u.value)
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(self._u))
+        mx = float(self._u.value)
+        self._getr(self.h, ct.byref(self._r))
+        return sm, mx, int(self._r.value)
+
+
+class ClockSampler:
+    """SM clock and clock-event reasons sampled while the timed region runs.
+
+    A background thread polls the source every `period` seconds, with one sample at entry and one
+    at exit as well, so a timed region of a few milliseconds still has samples.  The source is
+    NVML (read-only); without it, `nvidia-smi --query-gpu ... -lms 5` is read instead."""
+
+    # clock-event reason bits of NVML (nvml.h)
+    REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                   0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period=0.002, source=None):
         self.index = index
+        self.period = period
+        self.src = source
+        self.samples = []
         self.proc = None
+        self.lines = []
+        self.kind = None
+
+    def _poll(self):
+        import time as _t
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.src.sample())
+            except Exception:
+                return
+            _t.sleep(self.period)
 
     def __enter__(self):
+        import threading
+        if self.src is None:
+            try:
+                self.src = NvmlClocks(self.index)
+            except Exception:
+                self.src = None
+        if self.src is not None:
+            self.kind = "nvml"
+            self._stop = threading.Event()
+            try:
+                self.samples.append(self.src.sample())
+            except Exception:
+                pass
+            self._th = threading.Thread(target=self._poll, daemon=True)
+            self._th.start()
+            return self
         try:
+            self.kind = "nvidia-smi"
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.index), "-lms", "5"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
-        if self.proc is not None:
+        if self.src is not None and self.kind == "nvml":
+            self._stop.set()
+            self._th.join(timeout=2)
+            try:
+                self.samples.append(self.src.sample())
+            except Exception:
+                pass
+        elif self.proc is not None:
             self.proc.terminate()
             try:
                 out, _ = self.proc.communicate(timeout=5)
@@ -132,11 +214,15 @@ class ClockSampler:
                 self.proc.kill()
                 out = ""
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
-        else:
-            self.lines = []
 
     def summary(self):
         sm, mx, reasons = [], None, set()
+        for smhz, mmhz, bits in self.samples:
+            sm.append(smhz)
+            mx = mmhz
+            for b, nm in self.REASON_BITS.items():
+                if bits & b:
+                    reasons.add(nm)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -151,8 +237,9 @@ class ClockSampler:
                 if parts[4 + k].lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": self.kind}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": self.kind}
 
 
 def algorithmic_bytes_per_atom_step(mean_nbrs: float, precision: str = "mixed", rule: str = "vmax") -> float:
@@ -167,6 +254,24 @@ def algorithmic_bytes_per_atom_step(mean_nbrs: float, precision: str = "mixed", 
     if precision == "fp32":
         return 16 + 4 + 12 + 16 + 12 + ref + 4.0 * mean_nbrs
     return 32 + 4 + 24 + 24 + 24 + 24 + 32 + ref + 4.0 * mean_nbrs
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def cpu_oracle_rate(x, v, box, rc, steps, threads):
@@ -190,7 +295,7 @@ def run_gb300(args, rank, world, local_rank):
     x, v, geo = make_inputs(args.workload, rank, args.ncell)
     n = x.shape[0]
     s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
-                 rebuild_rule=RULE, **geo)
+                 rebuild_rule=RULE, props_every=args.props_every, **geo)
     if args.ctas_per_sm or args.nbr_batch or args.build_batch:
         s.set_tuning(ctas_per_sm=args.ctas_per_sm, nbr_batch=args.nbr_batch, build_batch=args.build_batch)
     tuned = None
@@ -296,7 +401,14 @@ def run_gb300(args, rank, world, local_rank):
                 steps_cpu = args.cpu_steps
                 rate, _ = cpu_oracle_rate(x, v, geo["box"], w["rc"], steps_cpu, threads)
                 sample = f"{steps_cpu} steps of the full {n}-atom system from its initial state"
-            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+            one = None
+            if args.workload != "batch512" and args.cpu_steps_1t > 0:
+                r1, s1 = cpu_oracle_rate(x, v, geo["box"], w["rc"], args.cpu_steps_1t, 1)
+                one = {"value": r1, "unit": UNIT, "cores": 1, "seconds": s1,
+                       "sample": f"{args.cpu_steps_1t} steps of the full {n}-atom system, one thread"}
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                   "cpu_model": cpu_model(), "nproc": os.cpu_count(), "single_thread": one,
+                   "note": "the FP64 oracle as written: OpenMP over atoms in its force loop, its kick-drift loop serial"}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -308,7 +420,16 @@ def run_gb300(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (state %.2f GB)" % (s.workspace_bytes / 1e9),
                        "mean_neighbours": mean_nbrs,
                        "rebuilds_per_100_steps": 100.0 * rebuilds_timed / max(s.nrep, 1) / args.steps,
-                       "cuda_graph": graph_mode},
+                       "cuda_graph": graph_mode,
+                       "props_every": args.props_every,
+                       "reductions": ("every step: max |v| (refresh criterion) and, fused into the step kernel, "
+                                      "U, K, virial, pressure and momentum into the device time series"
+                                      if args.props_every == 1 else
+                                      "every step: max |v| (refresh criterion); U, K, virial, pressure and "
+                                      "momentum fused into every %d-th step" % args.props_every
+                                      if args.props_every > 1 else
+                                      "every step: max |v| (refresh criterion) only; the energy/virial reductions "
+                                      "are the forms wca4m_mixed_props1/_props10 and the e2e loop")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (lambda b: None if b is None else b * n)(traffic_per_atom("k_step_sm<MD_MIXED>")),
@@ -344,12 +465,13 @@ def _event_ms(s, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune=True, rule="vmax"):
+def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune=True, rule="vmax",
+                 props_every=0):
     """Particle-steps/s of one form of the hot path, with its step-kernel roofline fraction."""
     from paper_2003_14061_gb300 import tune as gtune
     from paper_2003_14061_gb300.system import MDSystem
     s = MDSystem(x, v, device=dev, rc=rc, skin=skin, dt=DT, precision=precision, reorder_every=100,
-                 rebuild_rule=rule, **geo)
+                 rebuild_rule=rule, props_every=props_every, **geo)
     s.integrate(max(warmup // 2, 16))
     if tune:
         gtune.tune(s, steps=64)
@@ -369,7 +491,8 @@ def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune
     bpa = algorithmic_bytes_per_atom_step(mean_nbrs, precision, rule)
     achieved = bpa * n / (step_ms * 1e-3) / 1e9
     out = {"label": label, "value": n * steps / (ms * 1e-3), "unit": UNIT, "atoms": n, "replicas": s.nrep,
-           "steps": steps, "ms_per_step": ms / steps, "precision": precision, "mean_neighbours": mean_nbrs,
+           "steps": steps, "ms_per_step": ms / steps, "precision": precision, "props_every": props_every,
+           "mean_neighbours": mean_nbrs,
            "rebuilds_per_100_steps": 100.0 * sum(a["rebuilds"] - b["rebuilds"] for a, b in zip(p1, p0)) / s.nrep / steps,
            "kernel_ms_per_launch": step_ms, "tuning": s.tuning(),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -389,6 +512,13 @@ def measure_forms(args, dev):
     x, v, geo = make_inputs("wca4m")
     forms["wca4m_fp32"] = measure_form("WCA fcc 100^3, FP32 state", x, v, geo, dev, "fp32", WCA_RC, 0.4,
                                        args.form_steps, 200)
+    # the main workload with the energy/virial/momentum reductions (F2) fused into every step, and
+    # into every 10th step
+    forms["wca4m_mixed_props1"] = measure_form("WCA fcc 100^3, MIXED, U/K/W/P/momentum reduced every step", x, v,
+                                               geo, dev, "mixed", WCA_RC, 0.4, args.form_steps, 200, props_every=1)
+    forms["wca4m_mixed_props10"] = measure_form("WCA fcc 100^3, MIXED, U/K/W/P/momentum reduced every 10 steps", x,
+                                                v, geo, dev, "mixed", WCA_RC, 0.4, args.form_steps, 200,
+                                                props_every=10)
     # the main workload with the exact-displacement refresh rule (reads the positions at the last
     # rebuild every step)
     forms["wca4m_mixed_disp"] = measure_form("WCA fcc 100^3, MIXED, rebuild on max |x - x_ref| > skin/2", x, v, geo,
@@ -469,7 +599,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "atoms": x.shape[0]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -493,8 +624,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--phase-steps", type=int, default=400)
     ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--cpu-steps-1t", type=int, default=2, help="steps of the one-thread oracle timing (0: skip)")
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--props-every", type=int, default=1,
+                    help="steps between fused reductions of U, K, virial, pressure and momentum (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

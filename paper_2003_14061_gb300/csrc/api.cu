@@ -189,9 +189,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.rb_tiles = c.take<int32_t>(size_t(P.ntiles));
     a.cell_rep = c.take<int32_t>(size_t(P.ncells));
     a.rb_base = c.take<int32_t>(size_t(P.nrep));
-    a.tile_part = c.take<double>(size_t(P.ntiles) * NPROP);
     a.warp_part = c.take<double>(size_t(P.ntiles) * (TILE / 32) * NPROP);
-    a.tile_warps = c.take<int32_t>(size_t(P.ntiles));
     a.slice_part = c.take<double>(size_t(P.nrep) * PROPS_SPLIT * NPROP);
     a.rep = c.take<Rep>(size_t(P.nrep));
     a.rs = c.take<RepState>(size_t(P.nrep));

@@ -117,9 +117,7 @@ struct Arrays {
     int32_t* rb_tiles;        // tiles of the replicas rebuilding in this step
     int32_t* cell_rep;        // replica of every (global) cell
     int32_t* rb_base;         // per replica: its first entry in rb_tiles
-    double* tile_part;        // NPROP per tile
-    double* warp_part;        // NPROP per warp-tile (32 slots): the per-SM step kernel's partials
-    int32_t* tile_warps;      // per tile: warps whose partials are in (the fourth combines them)
+    double* warp_part;        // NPROP per warp of every tile (32 slots): the props partials
     double* slice_part;       // NPROP per (replica, slice) of the final sums
     // per replica
     Rep* rep;

@@ -22,6 +22,7 @@
 //   k_props_*  F2 and the other measured quantities: per-tile FP64 partials, then one CTA per
 //              replica sums them in a fixed order (deterministic).
 #include <algorithm>
+#include <type_traits>
 
 #include "gbmd_internal.cuh"
 
@@ -134,23 +135,28 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
 // FP64 state (v, x), MD_FP32 the FP32 velocity v32 and position pi; pn receives the FP32
 // cell-local position of step n+1.  FP32<->FP64 conversions run on the integer pipe (bit for bit
 // the hardware ones).  Returns |x_{n+1} - x_n|^2 measured on the FP32 positions (the
-// refresh metric unless the rule is DISP).  With PROPS, part receives u_i, |v|^2, the virial and
-// the momentum at step n.
+// refresh metric unless the rule is DISP).  With PROPS, part receives this atom's terms of the
+// props at step n in FP32 -- u_i, |v_n|^2, the virial and v_n -- which the warp sums in FP32 and
+// everything beyond the warp sums in FP64 (the MD_MIXED contract): v_n = v + c f from the FP32
+// rounding of the stored velocity, so the props cost no FP64 arithmetic (1/64 of the FP32 rate
+// on GB300).
 template <int MODE, bool PROPS>
 __device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const float4& pi, const AccF& a,
                                             double (&v)[3], double (&x)[3], float (&v32)[3], float (&pn)[3],
-                                            double (&part)[NPROP])
+                                            float (&part)[NPROP])
 {
     const float f[3] = {a.fx, a.fy, a.fz};
-    double vn2 = 0.0;
+    const float cf = float(S.c);
+    float vn2 = 0.0f;
     if (MODE == MD_MIXED) {
         const double kick = vhalf ? 2.0 * S.c : S.c;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const double fq = f32_to_f64(f[q]);
             if (PROPS) {
-                const double vn = vhalf ? fma(S.c, fq, v[q]) : v[q];
-                vn2 = fma(vn, vn, vn2);
+                const float vf = f64_to_f32(v[q]);
+                const float vn = vhalf ? fmaf(cf, f[q], vf) : vf;
+                vn2 = fmaf(vn, vn, vn2);
                 part[3 + q] = vn;
             }
             v[q] = fma(kick, fq, v[q]);
@@ -159,24 +165,23 @@ __device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const floa
         }
     } else {
         const float kick = float(vhalf ? 2.0 * S.c : S.c);
-        const float cf = float(S.c), dtf = float(S.dt);
+        const float dtf = float(S.dt);
         const float pc[3] = {pi.x, pi.y, pi.z};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             if (PROPS) {
                 const float vn = vhalf ? fmaf(cf, f[q], v32[q]) : v32[q];
-                const double vd = f32_to_f64(vn);
-                vn2 = fma(vd, vd, vn2);
-                part[3 + q] = vd;
+                vn2 = fmaf(vn, vn, vn2);
+                part[3 + q] = vn;
             }
             v32[q] = fmaf(kick, f[q], v32[q]);
             pn[q] = fmaf(dtf, v32[q], pc[q]);
         }
     }
     if (PROPS) {
-        part[0] = f32_to_f64(a.u);
+        part[0] = a.u;
         part[1] = vn2;
-        part[2] = f32_to_f64(a.w);
+        part[2] = a.w;
         part[NPROP - 1] = vn2;
     }
     // |x_{n+1} - x_n| = dt |v_{n+1/2}| from the FP32 copies of both positions (same cell frame);
@@ -232,63 +237,61 @@ __device__ __forceinline__ float tile_max(float v, float* sh)
     return m;
 }
 
-// Per-tile FP64 sums of the 7 additive quantities and the FP32 maximum of |v|^2.  The 8 doubles
+// Per-tile FP64 sums of the 7 additive quantities and the FP32 maximum of |v|^2.  The 8 values
+// (FP64 for MD_FP64 and the standalone reduction, FP32 in the MD_MIXED / MD_FP32 step kernels)
 // of each lane are reduced across the warp by reduce-scatter (each exchange halves the number of
 // quantities a lane carries, 4 + 2 + 1 adds, then 2 more over the last 4 lanes): 9 FP64 adds per
 // lane instead of 35 for a butterfly per quantity (FP64 runs at 1/64-1/72 of the FP32 rate on
 // GB300).
 // The in-warp part: lane 4q (q < NPROP - 1) ends with the warp's sum of quantity q, lane 0 also
 // with the warp's maximum of |v|^2 (returned in vm).
-__device__ __forceinline__ double warp_partials(double (&p)[NPROP], int& q, float& vm)
+template <class T>
+__device__ __forceinline__ T warp_partials(T (&p)[NPROP], int& q, float& vm)
 {
     const int lane = threadIdx.x & 31;
     vm = warp_max(float(p[NPROP - 1]));
-    p[NPROP - 1] = 0.0;
+    p[NPROP - 1] = T(0);
     const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-    double a4[4];
+    T a4[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const double keep = h16 ? p[4 + k] : p[k], give = h16 ? p[k] : p[4 + k];
+        const T keep = h16 ? p[4 + k] : p[k], give = h16 ? p[k] : p[4 + k];
         a4[k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
     }
-    double a2[2];
+    T a2[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const double keep = h8 ? a4[2 + k] : a4[k], give = h8 ? a4[k] : a4[2 + k];
+        const T keep = h8 ? a4[2 + k] : a4[k], give = h8 ? a4[k] : a4[2 + k];
         a2[k] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
     }
-    double a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
+    T a1 = (h4 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? a2[0] : a2[1], 4);
     a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
     a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
     q = (h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0);
     return a1;
 }
 
-// the NPROP values of one warp into dst[0..NPROP)
-__device__ __forceinline__ void warp_partials_store(double (&p)[NPROP], double* dst)
+// the NPROP values of one warp into dst[0..NPROP) (FP64; from FP32 lanes the warp's sums are
+// formed in FP32 and widened exactly)
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f32_to_f64(x); }
+
+template <class T>
+__device__ __forceinline__ void warp_partials_store(T (&p)[NPROP], double* dst)
 {
     const int lane = threadIdx.x & 31;
     int q;
     float vm;
-    const double a1 = warp_partials(p, q, vm);
-    if ((lane & 3) == 0 && q != NPROP - 1) dst[q] = a1;
-    if (lane == 0) dst[NPROP - 1] = double(vm);
+    const T a1 = warp_partials(p, q, vm);
+    if ((lane & 3) == 0 && q != NPROP - 1) dst[q] = widen(a1);
+    if (lane == 0) dst[NPROP - 1] = widen(vm);
 }
 
-// the tile's value of quantity k from its warps' values, in warp order
-__device__ __forceinline__ double combine_warps(const double* w, int k, int stride)
-{
-    double s = w[k];
-    for (int j = 1; j < TILE / 32; ++j) s = (k == NPROP - 1) ? fmax(s, w[j * stride + k]) : s + w[j * stride + k];
-    return s;
-}
-
-__device__ __forceinline__ void tile_partials(double (&p)[NPROP], double (*sh)[NPROP], double* out)
-{
-    warp_partials_store(p, sh[threadIdx.x >> 5]);
-    __syncthreads();
-    if (threadIdx.x < NPROP) out[threadIdx.x] = combine_warps(&sh[0][0], threadIdx.x, NPROP);
-}
+// Each warp of a tile stores its NPROP values at warp_part[(t * TILE / 32 + warp) * NPROP]; the
+// props kernel adds a tile's warps in warp order.  No fence or counter is needed between the
+// step kernel and that kernel (the launch boundary orders them), so a warp never waits for its
+// own stores.
+__device__ __forceinline__ double* warp_slot(const Arrays& A, int64_t warp_tile) { return A.warp_part + warp_tile * NPROP; }
 
 // Refresh criterion and step bookkeeping, run by one thread of the CTA that completed the last
 // tile of replica r in this launch.
@@ -358,7 +361,6 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
                                                  int use_cond, int stage_cap)
 {
     __shared__ float sh_max[TILE / 32];
-    __shared__ double sh_part[PROPS ? TILE / 32 : 1][NPROP];
     extern __shared__ __align__(16) float4 s_nb[];       // STG: staged neighbour positions
     __shared__ int4 sh_win[16];          // STG: per (o_y+1) + 4 (o_z+1): first slot, length, s_nb offset
     __shared__ uint64_t sh_bar;
@@ -464,11 +466,12 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
             }
         }
         float metric = 0.0f;                     // |v|^2 (VMAX) or |x - x_ref|^2 (DISP)
-        double part[NPROP];
+        using PT = typename std::conditional<MODE == MD_FP64, double, float>::type;
+        PT part[NPROP];
 #pragma unroll
-        for (int q = 0; q < NPROP; ++q) part[q] = 0.0;
+        for (int q = 0; q < NPROP; ++q) part[q] = PT(0);
         if (active) {
-            if (MODE == MD_FP64) {
+            if constexpr (MODE == MD_FP64) {
                 const double4_32a* pos = A.pos64[cur];
                 const double4_32a pi = pos[slot];
                 const AccD a = force_f64(A, S, R, pos, slot, pi);
@@ -573,10 +576,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
         }
         run_max = fmaxf(run_max, metric);
         run_tiles += 1;
-        if (PROPS) {
-            tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
-            __syncthreads();
-        }
+        if (PROPS) warp_partials_store(part, warp_slot(A, int64_t(t) * (TILE / 32) + (threadIdx.x >> 5)));
     }
     if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
     if (STG && stg_timeout) atomicOr(&A.g->err, ERR_TIMEOUT);
@@ -718,9 +718,9 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         const bool active = slot - R.slot0 < R.n;
         const int vhalf = A.rs[r].vhalf;
         float metric = 0.0f;                     // |v|^2 (VMAX) or |x - x_ref|^2 (DISP)
-        double part[NPROP];
+        float part[NPROP];
 #pragma unroll
-        for (int q = 0; q < NPROP; ++q) part[q] = 0.0;
+        for (int q = 0; q < NPROP; ++q) part[q] = 0.0f;
         if (active) {
             const float4 pi = __ldg(pos + slot);
             const AccF a = force_f32_rows<NB>(A, S, R, pos, slot, pi, min(c0, S.cap));
@@ -755,30 +755,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         }
         run_max = fmaxf(run_max, metric);
         run_cnt += 1;
-        if (PROPS) {
-            // the warp's partials; the tile's fourth warp to store them sums the four in warp
-            // order, as k_step's tile reduction does, so the props agree bit for bit
-            warp_partials_store(part, A.warp_part + int64_t(w0) * NPROP);
-            __threadfence();
-            __syncwarp();
-            int last = 0;
-            if (lane == 0) last = atomicAdd(A.tile_warps + t, 1) == TILE / 32 - 1;
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
-                __threadfence();
-                if (lane < NPROP) {
-                    const double* wp = A.warp_part + int64_t(t) * (TILE / 32) * NPROP;
-                    double y = __ldcg(wp + lane);
-#pragma unroll
-                    for (int j = 1; j < TILE / 32; ++j) {
-                        const double z = __ldcg(wp + j * NPROP + lane);
-                        y = (lane == NPROP - 1) ? fmax(y, z) : y + z;      // combine_warps' order
-                    }
-                    A.tile_part[int64_t(t) * NPROP + lane] = y;
-                }
-                if (lane == 0) A.tile_warps[t] = 0;
-            }
-        }
+        if (PROPS) warp_partials_store(part, warp_slot(A, w0));   // w0 = t * TILE / 32 + warp of the tile
         int w2 = -1;
         if (w1 >= 0) {
             // the rows of W below the next warp-tile's largest count into L2
@@ -827,7 +804,6 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
     __shared__ uint64_t bar[2];
     __shared__ float sh_max[TILE / 32];
     __shared__ int sh_mm[2][TILE / 32];
-    __shared__ double sh_part[PROPS ? TILE / 32 : 1][NPROP];
     const StageLayout SL = stage_layout(MODE, rows);
     const int nxt = cur ^ 1;
     const int per = (S.ntiles + gridDim.x - 1) / gridDim.x;
@@ -912,9 +888,9 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
         parity ^= 1u << st;
         const unsigned char* sb = ring + size_t(st) * SL.bytes;
         float metric = 0.0f;
-        double part[NPROP];
+        float part[NPROP];
 #pragma unroll
-        for (int q = 0; q < NPROP; ++q) part[q] = 0.0;
+        for (int q = 0; q < NPROP; ++q) part[q] = 0.0f;
         if (active && !timed_out) {
             const float4 pi = reinterpret_cast<const float4*>(sb + SL.pos)[threadIdx.x];
             const int mm = min(reinterpret_cast<const int32_t*>(sb + SL.cnt)[threadIdx.x], S.cap);
@@ -955,7 +931,7 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
         }
         run_max = fmaxf(run_max, metric);
         run_tiles += 1;
-        if (PROPS) tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
+        if (PROPS) warp_partials_store(part, warp_slot(A, int64_t(t) * (TILE / 32) + warp));
         // release the stage (every thread is past its reads of it), then refill it with tile t+2
         const int wm = warp_max_i(c2);
         if (lane == 0) sh_mm[st][warp] = wm;
@@ -995,7 +971,6 @@ __global__ void __launch_bounds__(TILE) k_forces(Arrays A, Scal S, int cur)
 template <int MODE>
 __global__ void __launch_bounds__(TILE) k_props_tiles(Arrays A, Scal S)
 {
-    __shared__ double sh_part[TILE / 32][NPROP];
     for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
         const int r = A.tile_rep[t];
         const Rep& R = A.rep[r];
@@ -1021,14 +996,14 @@ __global__ void __launch_bounds__(TILE) k_props_tiles(Arrays A, Scal S)
             part[2] = A.wvir[slot];
             part[NPROP - 1] = vn2;
         }
-        tile_partials(part, sh_part, A.tile_part + int64_t(t) * NPROP);
-        __syncthreads();
+        warp_partials_store(part, warp_slot(A, int64_t(t) * (TILE / 32) + (threadIdx.x >> 5)));
     }
 }
 
-// Final sums, two fixed-order levels: PROPS_SPLIT CTAs per replica each add a contiguous slice
-// of the replica's tile partials, then one warp per replica adds the slices and applies the
-// constant factors (U = sum u_i / 2, K = m sum v^2 / 2, W = sum w_i / 2, P = m sum v).
+// Final sums, in a fixed order: PROPS_SPLIT CTAs per replica each add a contiguous slice of the
+// replica's tiles (each tile the sum of its warps' partials in warp order), then one warp per
+// replica adds the slices and applies the constant factors (U = sum u_i / 2, K = m sum v^2 / 2,
+// W = sum w_i / 2, P = m sum v).
 __global__ void __launch_bounds__(256) k_props_slices(Arrays A, Scal S)
 {
     __shared__ double sh[256][NPROP];
@@ -1040,10 +1015,14 @@ __global__ void __launch_bounds__(256) k_props_slices(Arrays A, Scal S)
 #pragma unroll
     for (int q = 0; q < NPROP; ++q) acc[q] = 0.0;
     for (int k = k0 + int(threadIdx.x); k < k1; k += blockDim.x) {
-        const double* p = A.tile_part + int64_t(R.tile0 + k) * NPROP;
+        const double* w = A.warp_part + int64_t(R.tile0 + k) * (TILE / 32) * NPROP;
 #pragma unroll
-        for (int q = 0; q < NPROP - 1; ++q) acc[q] += p[q];
-        acc[NPROP - 1] = fmax(acc[NPROP - 1], p[NPROP - 1]);
+        for (int q = 0; q < NPROP; ++q) {
+            double y = w[q];
+#pragma unroll
+            for (int j = 1; j < TILE / 32; ++j) y = (q == NPROP - 1) ? fmax(y, w[j * NPROP + q]) : y + w[j * NPROP + q];
+            acc[q] = (q == NPROP - 1) ? fmax(acc[q], y) : acc[q] + y;
+        }
     }
 #pragma unroll
     for (int q = 0; q < NPROP; ++q) sh[threadIdx.x][q] = acc[q];

@@ -335,7 +335,11 @@ def test_series_ring_and_latest_row():
     e.integrate(9)
     p = e.props()[0]
     assert p["step"] == 9
-    assert abs(r9[1] - p["U"]) <= 1e-9 * abs(p["U"]) and abs(r9[2] - p["K"]) <= 1e-9 * abs(p["K"])
+    # the step kernel sums each warp's terms in FP32 (the MD_MIXED contract: FP64 beyond a warp),
+    # the standalone reduction in FP64 throughout: they agree to the energy bar
+    n = e.n
+    assert abs(r9[1] - p["U"]) / n <= 1e-7 and abs(r9[2] - p["K"]) / n <= 1e-7
+    assert abs(r9[3] - p["virial"]) / n <= 1e-6
 
 
 def test_rebuild_rules():
