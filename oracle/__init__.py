@@ -69,9 +69,10 @@ def _load():
         lib.orc_param_grads.argtypes = [i64, dp, dp, P, dp, dp, dp, dp]
         lib.orc_adjoint.argtypes = [i64, dp, dp, dp, P, d, d, i64, dp, dp, dp, dp, dp, dp]
         lib.orc_loss.argtypes = [i64, dp, dp, dp, P, d, d, i64, dp]
+        lib.orc_dynamics.argtypes = [i64, dp, dp, dp, P, d, d, i64, i32, i32, i32, dp, dp, dp]
         for name in ("orc_forces_brute", "orc_forces_cells", "orc_force_on_atoms", "orc_cells",
                      "orc_cell_order", "orc_neighbours", "orc_neighbours_sample", "orc_props", "orc_run", "orc_force_jvp",
-                     "orc_param_grads", "orc_adjoint", "orc_loss"):
+                     "orc_param_grads", "orc_adjoint", "orc_loss", "orc_dynamics"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -275,3 +276,21 @@ def loss(x0, v0, box, p: Pot, mass=1.0, dt=0.005, nsteps=1):
     _check(_load().orc_loss(x0.shape[0], _ptr(x0), _ptr(v0), _ptr(box), ctypes.byref(p), float(mass),
                             float(dt), int(nsteps), ctypes.byref(out)), "loss")
     return out.value
+
+
+def dynamics(x0, v0, box, p: Pot, mass=1.0, dt=0.005, nsamples=1, every=1, nlag=1, origin_every=1):
+    """VACF and MSD per atom over lags 0..nlag-1 (samples every `every` steps, a new origin every
+    `origin_every` samples): (vacf [nlag], msd [nlag], counts [nlag]) as averages per atom and
+    origin, and the number of origins that reached each lag."""
+    x0 = _f64(x0, (-1, 3))
+    v0 = _f64(v0, (-1, 3))
+    box = _f64(box, (3,))
+    n = x0.shape[0]
+    vacf = np.zeros(int(nlag))
+    msd = np.zeros(int(nlag))
+    cnt = np.zeros(int(nlag), dtype=np.int64)
+    _check(_load().orc_dynamics(n, _ptr(x0), _ptr(v0), _ptr(box), ctypes.byref(p), float(mass), float(dt),
+                                int(nsamples), int(every), int(nlag), int(origin_every), _ptr(vacf), _ptr(msd),
+                                _ptr(cnt)), "dynamics")
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return vacf / (n * cnt), msd / (n * cnt), cnt

@@ -32,6 +32,9 @@
  *   orc_adjoint         -- reverse-mode derivative of the trajectory loss
  *                          L = (1/S) sum_{n=1..S} U(x_n) + |v_S|^2 through the leapfrog steps,
  *                          with every state stored (no checkpointing).
+ *   orc_dynamics        -- velocity autocorrelation and mean-square displacement of atoms
+ *                          followed by identity (Sec. 4.1 items 1 and 7), from orc_run's
+ *                          trajectory, over several time origins.
  *
  * Parity notes: the potential, forces, energies, integrator and adjoint are pinned by closed
  * forms, brute force, lattice sums, invariants and finite differences in the CPU test suite.
@@ -877,5 +880,82 @@ int orc_loss(int64_t n, const double* x0, const double* v0, const double* box, c
     }
     if (!rc) *loss_out = loss + orc_dot((int64_t)n3, v, v);
     free(x); free(v); free(f);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Velocity autocorrelation and mean-square displacement of atoms followed by their permanent  */
+/* ids (Sec. 4.1 item 1: atoms keep identities through reordering; Sec. 4.1 item 7: the VACF   */
+/* of the SP fluid at rho = 1.0, whose oscillations show the atoms are caged).                 */
+/* The trajectory is orc_run's (KDK leapfrog, forces from the definition).  A sample is taken  */
+/* at step 0 and after every `every` steps, at integer-step velocities.  Sample s starts a new  */
+/* time origin when s is a multiple of origin_every, and every origin is followed for nlag     */
+/* samples (lags 0 .. nlag-1):                                                                 */
+/*   vacf[k] = sum over origins t0 reaching lag k, and atoms i, of v_i(t0) . v_i(t0 + k T)     */
+/*   msd[k]  = the same sum of |r_i(t0 + k T) - r_i(t0)|^2,   T = every dt,                    */
+/* with r_i unwrapped: r_i(t) - r_i(t0) is the sum of the drifts dt v_{n+1/2} in between.      */
+/* counts[k] = number of origins that reached lag k; the averages per atom are                 */
+/* vacf[k] / (n counts[k]) and msd[k] / (n counts[k]).  nsamples = samples taken in total.     */
+/* ------------------------------------------------------------------------------------------ */
+int orc_dynamics(int64_t n, const double* x0, const double* v0, const double* box, const orc_pot* p,
+                 double mass, double dt, int64_t nsamples, int32_t every, int32_t nlag,
+                 int32_t origin_every, double* vacf, double* msd, int64_t* counts)
+{
+    if (n <= 0 || !x0 || !v0 || !box || !p || mass <= 0.0 || nsamples <= 0 || every <= 0 || nlag <= 0 ||
+        origin_every <= 0 || !vacf || !msd || !counts)
+        return ORC_ERR_ARG;
+    size_t n3 = 3 * (size_t)n;
+    int32_t norg = (nlag + origin_every - 1) / origin_every;     /* origins alive at once */
+    double* x = (double*)malloc(sizeof(double) * n3);
+    double* v = (double*)malloc(sizeof(double) * n3);
+    double* f = (double*)malloc(sizeof(double) * n3);
+    double* dr = (double*)calloc(n3 * (size_t)norg, sizeof(double));    /* displacement since origin */
+    double* vo = (double*)calloc(n3 * (size_t)norg, sizeof(double));    /* velocity at the origin */
+    int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)norg);   /* sample index of the origin */
+    if (!x || !v || !f || !dr || !vo || !start) {
+        free(x); free(v); free(f); free(dr); free(vo); free(start);
+        return ORC_ERR_MEM;
+    }
+    for (int32_t b = 0; b < norg; ++b) start[b] = -1;
+    for (int32_t k = 0; k < nlag; ++k) { vacf[k] = 0.0; msd[k] = 0.0; counts[k] = 0; }
+    memcpy(x, x0, sizeof(double) * n3);
+    memcpy(v, v0, sizeof(double) * n3);
+    double c = dt / (2.0 * mass), U, W;
+    int rc = orc_forces_cells(n, x, box, p, f, NULL, &U, &W);
+    for (int64_t s = 0; s < nsamples && !rc; ++s) {
+        if (s > 0) {
+            for (int32_t q = 0; q < every && !rc; ++q) {
+                for (size_t k = 0; k < n3; ++k) {
+                    v[k] += c * f[k];
+                    double drift = dt * v[k];
+                    for (int32_t b = 0; b < norg; ++b) dr[(size_t)b * n3 + k] += drift;
+                    x[k] = orc_wrap(x[k] + drift, box[k % 3]);
+                }
+                rc = orc_forces_cells(n, x, box, p, f, NULL, &U, &W);
+                for (size_t k = 0; k < n3; ++k) v[k] += c * f[k];
+            }
+            if (rc) break;
+        }
+        if (s % origin_every == 0) {                   /* a new origin in the oldest slot */
+            int32_t b = (int32_t)((s / origin_every) % norg);
+            start[b] = s;
+            memcpy(&vo[(size_t)b * n3], v, sizeof(double) * n3);
+            memset(&dr[(size_t)b * n3], 0, sizeof(double) * n3);
+        }
+        for (int32_t b = 0; b < norg; ++b) {
+            if (start[b] < 0) continue;
+            int64_t lag = s - start[b];
+            if (lag >= nlag) continue;
+            double cv = 0.0, cm = 0.0;
+            for (size_t k = 0; k < n3; ++k) {
+                cv += v[k] * vo[(size_t)b * n3 + k];
+                cm += dr[(size_t)b * n3 + k] * dr[(size_t)b * n3 + k];
+            }
+            vacf[lag] += cv;
+            msd[lag] += cm;
+            counts[lag] += 1;
+        }
+    }
+    free(x); free(v); free(f); free(dr); free(vo); free(start);
     return rc;
 }

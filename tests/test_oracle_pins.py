@@ -550,3 +550,43 @@ def test_adjoint_single_step_closed_form():
     want = -dt * f1 + 2 * v1 + 2 * c * dt * oracle.force_jvp(x1, box, wca(), v1)
     _, _, _, gv, _, _ = oracle.adjoint(x, v, box, wca(), dt=dt, nsteps=1)
     assert np.abs(gv - want).max() <= 1e-12 * np.abs(want).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# velocity autocorrelation and mean-square displacement (Sec. 4.1 items 1 and 7)
+# ---------------------------------------------------------------------------------------------
+def test_dynamics_free_flight_closed_form():
+    # atoms on a grid of spacing 3 moving at most 0.3 in the run stay farther apart than r_c: no
+    # force acts, so v_i(t) = v_i(0) and r_i(t) - r_i(0) = v_i t: VACF(k) = <v^2> and MSD(k) =
+    # <v^2> (k T)^2, T = every dt, for every lag, however the atoms wrap through the box
+    g = np.stack(np.meshgrid(*[np.arange(6)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    box = np.array([18.0, 18.0, 18.0])
+    x = (g + 0.5) * 3.0
+    v = np.random.default_rng(8).uniform(-0.5, 0.5, x.shape)
+    x[0] = [17.95, 1.5, 1.5]                        # crosses x = L at once
+    v[0] = [0.5, 0.0, 0.0]
+    every, nlag, origin_every, nsamples = 4, 12, 3, 30
+    vacf, msd, cnt = oracle.dynamics(x, v, box, wca(), dt=0.005, nsamples=nsamples, every=every, nlag=nlag,
+                                     origin_every=origin_every)
+    v2 = float((v ** 2).sum(1).mean())
+    T = every * 0.005
+    assert np.allclose(vacf, v2, rtol=1e-13)
+    assert np.allclose(msd, v2 * (np.arange(nlag) * T) ** 2, rtol=1e-11, atol=1e-16)
+    # origins at samples 0, 3, ..., 27; lag k is reached by the origins with start + k < nsamples
+    starts = np.arange(0, nsamples, origin_every)
+    assert np.array_equal(cnt, [(starts + k < nsamples).sum() for k in range(nlag)])
+
+
+def test_dynamics_caged_vacf_goes_negative():
+    # Sec. 4.1 item 7: in the SP fluid at rho = 1.0 the VACF oscillates -- each atom bounces off
+    # the cage of its neighbours -- so it turns negative within a fraction of a time unit; at
+    # lag 0 it is <v^2> = 3T at the state's temperature
+    x, box = inputs.fcc_lattice(5, 1.0)
+    v = inputs.maxwell(x.shape[0], 1.0, seed=9)
+    x, v = _equilibrate(x, v, box, wca(), 1.0, 400)
+    vacf, msd, cnt = oracle.dynamics(x, v, box, wca(), dt=0.005, nsamples=121, every=1, nlag=100, origin_every=5)
+    t_vmin = int(np.argmin(vacf))
+    assert vacf[0] == pytest.approx(3.0, rel=0.15)
+    assert vacf[t_vmin] < -0.05 * vacf[0] and 0.05 < t_vmin * 0.005 < 0.4
+    assert np.all(np.diff(msd[:20]) > 0)             # displacements grow at first ...
+    assert msd[1] == pytest.approx(vacf[0] * 0.005 ** 2, rel=0.05)   # ... ballistically
