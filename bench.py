@@ -466,14 +466,16 @@ def _event_ms(s, fn):
 
 
 def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune=True, rule="vmax",
-                 props_every=0):
+                 props_every=0, fixed=None):
     """Particle-steps/s of one form of the hot path, with its step-kernel roofline fraction."""
     from paper_2003_14061_gb300 import tune as gtune
     from paper_2003_14061_gb300.system import MDSystem
     s = MDSystem(x, v, device=dev, rc=rc, skin=skin, dt=DT, precision=precision, reorder_every=100,
                  rebuild_rule=rule, props_every=props_every, **geo)
     s.integrate(max(warmup // 2, 16))
-    if tune:
+    if fixed:
+        s.set_tuning(**fixed)
+    elif tune:
         gtune.tune(s, steps=64)
     s.integrate(max(warmup // 2, 16))
     p0 = s.props()
@@ -489,6 +491,8 @@ def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune
     step_ms = ph["step"][0] / max(ph["step"][1], 1)
     peak, kind = load_peaks()
     bpa = algorithmic_bytes_per_atom_step(mean_nbrs, precision, rule)
+    if fixed and fixed.get("step_kernel") == 4:
+        bpa = algorithmic_bytes_per_atom_step(0.0, precision, rule) - 4.0    # no W and no neighbour counts
     achieved = bpa * n / (step_ms * 1e-3) / 1e9
     out = {"label": label, "value": n * steps / (ms * 1e-3), "unit": UNIT, "atoms": n, "replicas": s.nrep,
            "steps": steps, "ms_per_step": ms / steps, "precision": precision, "props_every": props_every,
@@ -500,6 +504,51 @@ def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune
            "energy_per_atom": float(np.average([p["E_per_atom"] for p in p1], weights=s.n_rep))}
     s.close()
     return out
+
+
+def measure_dynamics(dev, n_edge=100, every=10, nsamples=100, nlag=50, origin_every=10):
+    """VACF, MSD and the self-diffusion coefficient of the SP fluid at density 1.0, T = 1, with
+    the throughput of the steps and samples together.  The start is the paper's (Sec. 3.1): a
+    simple cubic grid (spacing 1.0 < r_c, so it melts), brought to T = 1 by rescaling the
+    velocities every 100 steps for 500 steps before the measurement."""
+    from paper_2003_14061_gb300 import inputs
+    from paper_2003_14061_gb300.system import MDSystem
+    x, box = inputs.cubic_lattice(n_edge, 1.0)
+    v = inputs.maxwell(x.shape[0], 1.0, 7)
+    s = MDSystem(x, v, box, device=dev, rc=WCA_RC, skin=0.4, dt=DT, precision="mixed", reorder_every=100)
+    for _ in range(5):
+        s.integrate(100)
+        xs, vs, _ = s.state()
+        vs -= vs.mean(0)
+        vs *= math.sqrt(3.0 * (vs.shape[0] - 1) / float((vs * vs).sum()))
+        s.set_state(xs, vs)
+    s.integrate(100)
+    T_start = float(s.props()[0]["K"]) * 2.0 / (3.0 * (s.n - 1))
+    s.dyn_begin(nlag, origin_every)
+
+    def loop():
+        for k in range(nsamples):
+            if k:
+                s.integrate(every)
+            s.dyn_sample()
+
+    ms = _event_ms(s, loop)
+    vacf, msd, cnt = s.dyn_result()
+    n = s.n
+    T = every * DT
+    lags = np.arange(nlag) * T
+    half = nlag // 2
+    slope = np.polyfit(lags[half:], msd[half:], 1)[0]
+    kmin = int(np.argmin(vacf))
+    s.close()
+    steps = (nsamples - 1) * every
+    return {"label": "SP fluid rho = 1.0, T = 1 (simple cubic %d^3 start, melted) = %d atoms: VACF and MSD every %d "
+                     "steps" % (n_edge, n, every), "temperature_at_start": T_start,
+            "value": n * steps / (ms * 1e-3), "unit": UNIT, "steps": steps, "samples": nsamples,
+            "ms_per_step_with_samples": ms / steps, "vacf0": float(vacf[0]), "vacf_min": float(vacf[kmin]),
+            "vacf_min_time": float(lags[kmin]), "diffusion_D": float(slope / 6.0),
+            "msd_last": float(msd[-1]), "lag_time": T, "origins_at_last_lag": int(cnt[-1]),
+            "vacf": [round(float(a), 6) for a in vacf], "msd": [round(float(a), 6) for a in msd]}
 
 
 def measure_forms(args, dev):
@@ -519,6 +568,11 @@ def measure_forms(args, dev):
     forms["wca4m_mixed_props10"] = measure_form("WCA fcc 100^3, MIXED, U/K/W/P/momentum reduced every 10 steps", x,
                                                 v, geo, dev, "mixed", WCA_RC, 0.4, args.form_steps, 200,
                                                 props_every=10)
+    # the list-free step kernel (no neighbour matrix; the cell-block alternative of Sec. 4.2 item
+    # 1), A/B against the neighbour-matrix kernel on the main workload
+    forms["wca4m_mixed_list_free"] = measure_form("WCA fcc 100^3, MIXED, list-free step kernel (27 cells every step)",
+                                                  x, v, geo, dev, "mixed", WCA_RC, 0.4, args.form_steps, 200,
+                                                  fixed=dict(step_kernel=4, ctas_per_sm=8))
     # the main workload with the exact-displacement refresh rule (reads the positions at the last
     # rebuild every step)
     forms["wca4m_mixed_disp"] = measure_form("WCA fcc 100^3, MIXED, rebuild on max |x - x_ref| > skin/2", x, v, geo,
@@ -534,6 +588,9 @@ def measure_forms(args, dev):
     x, v, geo = make_inputs("batch512")
     forms["batch512_mixed"] = measure_form(w["desc"], x, v, geo, dev, "mixed", w["rc"], w["skin"],
                                            args.form_steps, 200)
+    # physics measurement: the SP fluid at density 1.0 (Sec. 4.1 item 7), VACF and MSD of atoms
+    # followed by their ids, sampled every 10 steps over 1000 steps
+    forms["sp_rho1_dynamics"] = measure_dynamics(dev)
     # FP64 cell list (skin 0, rebuilt every step), 2048 atoms: L2-resident, steps/s is the figure
     xl, box = inputs.fcc_lattice(8, 0.8)
     vl = inputs.maxwell(xl.shape[0], 1.0, 1)
@@ -550,7 +607,7 @@ def measure_forms(args, dev):
     va = inputs.maxwell(32000, 1.0, seed=6)
     s = MDSystem(xa, va, boxa, device=dev, rc=WCA_RC, skin=0.4, dt=DT, precision="mixed")
     from paper_2003_14061_gb300 import tune as gtune
-    gtune.tune(s, steps=64)                                # launch shapes for this 32k-atom system
+    gtune.tune(s, steps=64, step_kernels=(1, 2, 3))        # launch shapes for this 32k-atom system
     s.adjoint(400, 20)                                     # warm-up (workspace, graphs, lazy loads)
     import torch
     torch.cuda.synchronize()

@@ -217,7 +217,11 @@ typedef struct {
     int32_t build_batch;     /* neighbour build: 2 or 4 = one thread per atom loading that many
                                 candidates together; 32 = one warp per cell, each row of
                                 candidates staged once in shared memory (for cells of tens of
-                                atoms) */
+                                atoms); 1 = one thread per atom over half-side sub-cells, the
+                                atoms counting-sorted by sub-cell and only the sub-cells within
+                                reach scanned (about half the candidates).  The neighbour sets
+                                are the same for every choice; the order within a column of W
+                                (and so the summation order of a force) follows the choice */
     int32_t use_graph;       /* 1: md_integrate replays captured CUDA graphs; 2: direct launches */
     int32_t step_kernel;     /* fused step kernel (MD_MIXED, MD_FP32): 1 = each thread loads its
                                 atom's state and W column; warps take 32-atom warp-tiles from
@@ -229,7 +233,13 @@ typedef struct {
                                 neighbour positions first copied into
                                 shared memory by cp.async.bulk (one slot window per row of
                                 neighbour cells; compact when atoms are reordered at every
-                                rebuild, reorder_every = 0) */
+                                rebuild, reorder_every = 0);
+                                4 = no neighbour matrix (the cell-block alternative of Sec. 4.2
+                                item 1): every atom of the 27 cells around an atom is tested
+                                against r_c each step, two at a time in packed FP32x2; atoms are
+                                then reordered by cell at every rebuild and W is not built
+                                (md_get_neighbours reports the last W built; md_adjoint refuses
+                                this kernel) */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);
@@ -256,6 +266,31 @@ int md_get_tuning(const md_system* s, md_tuning* t);
 size_t md_adjoint_workspace_bytes(const md_system* s, int32_t nsteps, int32_t ckpt_every);
 int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, int32_t ckpt_every, double* loss,
                double* dL_deps, double* dL_dsigma, double* dL_dv0);
+
+/* Velocity autocorrelation and mean-square displacement of atoms followed by their permanent
+ * ids (Sec. 4.1 item 1: ids survive the reorders; Sec. 4.1 item 7: the VACF of the soft-sphere
+ * fluid at density 1.0 oscillates as atoms are caged).  md_dyn_begin starts a measurement in a
+ * caller-owned device buffer; every md_dyn_sample takes one sample at the current state (wrapped
+ * positions, velocities at the integer step; it evaluates the forces for them), the caller
+ * advancing the system between samples by a fixed number of steps T.  Sample s starts a new
+ * time origin when s is a multiple of origin_every, and each origin is followed for nlag samples
+ * (lags 0 .. nlag-1, at most 8 origins at once: ceil(nlag / origin_every) <= 8).  md_dyn_get
+ * returns, for each lag k,
+ *     vacf[k] = < v_i(t0) . v_i(t0 + k T) >,   msd[k] = < |r_i(t0 + k T) - r_i(t0)|^2 >
+ * averaged over all atoms (of all replicas) and over the origins that reached lag k
+ * (counts[k]).  r is unwrapped from consecutive samples by the minimum image, so an atom must
+ * move less than half a box side between two samples.  Sums are per CTA in FP64, added in a
+ * fixed order.  The self-diffusion coefficient is the slope of msd / 6 at long lags.
+ *   d_work : md_dyn_workspace_bytes(s, nlag, origin_every) bytes of device memory, 256-byte
+ *            aligned, owned by the caller and untouched by other calls (per-atom velocities and
+ *            displacements of every origin, indexed by id).
+ *   vacf, msd : host [nlag] doubles (may be NULL); counts: host [nlag] int64 (may be NULL).
+ * md_dyn_sample queues work and does not wait; md_dyn_get waits.  A new md_dyn_begin restarts the
+ * measurement. */
+size_t md_dyn_workspace_bytes(const md_system* s, int32_t nlag, int32_t origin_every);
+int md_dyn_begin(md_system* s, void* d_work, size_t work_bytes, int32_t nlag, int32_t origin_every);
+int md_dyn_sample(md_system* s);
+int md_dyn_get(md_system* s, double* vacf, double* msd, int64_t* counts);
 
 /* Per-phase timing (the breakdown of Table 2 of the paper: neighbour matrix, forces +
  * integration, layer/cell assignment, reorder, energy).  With timing enabled, every phase is

@@ -28,6 +28,7 @@ EXPORTS = (
     "md_nrep", "md_natoms", "md_nbr_capacity", "md_cells_per_axis", "md_set_tuning", "md_get_tuning",
     "md_destroy", "md_last_error", "md_set_timing", "md_get_timing", "md_forces_static",
     "md_adjoint_workspace_bytes", "md_adjoint", "md_props_latest", "md_debug_set_error",
+    "md_dyn_workspace_bytes", "md_dyn_begin", "md_dyn_sample", "md_dyn_get",
 )
 NPHASE = 6
 PHASES = ("step", "bin", "reorder", "build", "props", "other")
@@ -121,6 +122,10 @@ def lib(build_if_missing: bool = True):
             "md_adjoint": (ctypes.c_int, [vp, vp, sz, i32, i32, vp, vp, vp, vp]),
             "md_props_latest": (ctypes.c_int, [vp, vp]),
             "md_debug_set_error": (ctypes.c_int, [vp, i32]),
+            "md_dyn_workspace_bytes": (sz, [vp, i32, i32]),
+            "md_dyn_begin": (ctypes.c_int, [vp, vp, sz, i32, i32]),
+            "md_dyn_sample": (ctypes.c_int, [vp]),
+            "md_dyn_get": (ctypes.c_int, [vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbmd.so")
-SOURCES = ["api.cu", "kernels_rebuild.cu", "kernels_step.cu", "kernels_adjoint.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_rebuild.cu", "kernels_step.cu", "kernels_adjoint.cu", "kernels_dyn.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

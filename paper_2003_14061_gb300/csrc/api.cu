@@ -177,6 +177,13 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.perm = c.take<int32_t>(ns);
     if (!f64) a.psort = c.take<float4>(ns);
     if (!f64) a.tile_win = c.take<int2>(size_t(P.ntiles) * 9);
+    if (!f64) {
+        const size_t nsub = size_t(8) * size_t(P.ncells);
+        a.psub = c.take<float4>(ns);
+        a.scount = c.take<int32_t>(nsub);
+        a.sstart = c.take<int32_t>(nsub + 1);
+        a.schunk = c.take<int32_t>((nsub + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    }
     if (!f32) for (int q = 0; q < 3; ++q) a.tmp_d[q] = c.take<double>(ns);
     for (int q = 0; q < 3; ++q) a.tmp_v[q] = c.take<double>(ns);
     for (int q = 0; q < 2; ++q) a.tmp_i[q] = c.take<int32_t>(ns);
@@ -190,7 +197,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.cell_rep = c.take<int32_t>(size_t(P.ncells));
     a.rb_base = c.take<int32_t>(size_t(P.nrep));
     a.warp_part = c.take<double>(size_t(P.ntiles) * (TILE / 32) * NPROP);
-    a.slice_part = c.take<double>(size_t(P.nrep) * PROPS_SPLIT * NPROP);
+    a.slice_part = c.take<double>(size_t(P.nrep) * PROPS_SPLIT_MAX * NPROP);
     a.rep = c.take<Rep>(size_t(P.nrep));
     a.rs = c.take<RepState>(size_t(P.nrep));
     a.props = c.take<md_props>(size_t(P.nrep));
@@ -258,6 +265,13 @@ struct md_system {
     };
     std::vector<AdjGraph> adj_graphs;
     int64_t host_series_rows = 0;     // series rows issued (props steps since creation/clear)
+    // VACF / MSD measurement (md_dyn_*): buffers in the caller's d_work, origins kept on the host
+    bool dyn_on = false;
+    DynView dyn{};
+    int32_t dyn_nlag = 0, dyn_every = 0, dyn_norg = 0;
+    int64_t dyn_samples = 0;
+    int64_t dyn_start[DYN_MAX_ORG] = {0};
+    std::vector<int64_t> dyn_counts;
     cudaStream_t aux = nullptr;       // captures the IF-node bodies
     cudaStream_t gstream = nullptr;   // captures and replays the graphs (the caller's stream may be
                                       // the legacy default stream, which cannot be captured)
@@ -353,6 +367,14 @@ void fill_scal(md_system* s)
     S.reorder_every = p.reorder_every;
     S.series_cap = P.series_cap;
     S.shift = p.shift_energy;
+    S.nsub = int64_t(8) * P.ncells;
+    S.nschunks = int32_t((S.nsub + SCAN_CHUNK - 1) / SCAN_CHUNK);
+    {
+        // each CTA of the props reduction adds about 128 warp partials per thread pass
+        int32_t max_tiles = 1;
+        for (const Rep& R : P.reps) max_tiles = std::max(max_tiles, R.ntiles);
+        S.props_split = std::max(1, std::min(PROPS_SPLIT_MAX, (max_tiles + 31) / 32));
+    }
     S.dt = p.dt;
     S.mass = p.mass;
     S.c = p.dt / (2.0 * p.mass);
@@ -408,6 +430,8 @@ int apply_tuning(md_system* s)
     s->L.nbr_batch = s->tune.nbr_batch;
     s->L.build_batch = s->tune.build_batch;
     s->L.step_kernel = (s->S.mode == MD_FP64) ? 1 : s->tune.step_kernel;
+    // the list-free kernel reads each row of cells as a run of slots: atoms reorder at every rebuild
+    s->S.reorder_every = (s->L.step_kernel == 4) ? 0 : s->p.reorder_every;
     bulk_shape(s->S, per_sm, s->smem_per_sm, s->smem_per_cta, &s->L.bulk_rows, &s->L.bulk_smem);
     stage_shape(per_sm, s->smem_per_sm, &s->L.stage_cap, &s->L.stage_smem);
     s->L.ctas_req = per_sm;
@@ -722,7 +746,7 @@ int md_integrate(md_system* s, int32_t nsteps)
     if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
     if (nsteps < 0) return fail(MD_ERR_INVALID_ARG, "nsteps < 0");
     if (s->binned_fresh) {      // a md_bin_cells without md_build_neighbours: finish the rebuild
-        Phase t(s, MD_PHASE_BUILD, 3);
+        Phase t(s, MD_PHASE_BUILD, build_kernels(s->S, s->L));
         GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
         s->binned_fresh = false;
     }
@@ -742,7 +766,7 @@ int md_integrate(md_system* s, int32_t nsteps)
                 const int rc = capture_graph(s, s->cur, G, mask, &exec);
                 if (rc) return rc;
             }
-            Phase t(s, MD_PHASE_STEP, G + 2 * __builtin_popcount(mask));
+            Phase t(s, MD_PHASE_STEP, G + __builtin_popcount(mask));
             const int rc = replay(s, exec);
             if (rc) return rc;
             k += G;
@@ -755,7 +779,7 @@ int md_integrate(md_system* s, int32_t nsteps)
         const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
         if (props) s->host_series_rows += 1;
         {
-            Phase t(s, MD_PHASE_STEP, props ? 3 : 1);
+            Phase t(s, MD_PHASE_STEP, props ? 2 : 1);
             GBMD_CUDA(launch_step(s->A, s->S, s->L, s->cur, props));
         }
         s->cur ^= 1;
@@ -768,7 +792,7 @@ int md_integrate(md_system* s, int32_t nsteps)
             GBMD_CUDA(launch_reorder(s->A, s->S, s->L, s->cur));
         }
         {
-            Phase t(s, MD_PHASE_BUILD, 3);
+            Phase t(s, MD_PHASE_BUILD, build_kernels(s->S, s->L));
             GBMD_CUDA(launch_build_only(s->A, s->S, s->L, s->cur));
         }
         s->host_step += 1;
@@ -791,7 +815,7 @@ int md_get_timing(md_system* s, double* ms, int64_t* calls, int64_t* launches)
         // rebuild sequences inside graphs ran only when their IF node opened: count them here
         long long gr = 0;
         GBMD_CUDA(cudaMemcpy(&gr, &s->A.g->graph_rebuilds, sizeof(gr), cudaMemcpyDeviceToHost));
-        s->launches[MD_PHASE_BUILD] += REBUILD_KERNELS * (gr - s->graph_rebuilds_seen);
+        s->launches[MD_PHASE_BUILD] += (REBUILD_KERNELS - 3 + build_kernels(s->S, s->L)) * (gr - s->graph_rebuilds_seen);
         s->graph_rebuilds_seen = gr;
     }
     for (auto& pr : s->pending) {
@@ -817,7 +841,7 @@ int md_reduce_props(md_system* s, md_props* out)
 {
     if (!s || !out) return fail(MD_ERR_INVALID_ARG, "system or out is NULL");
     {
-        Phase t(s, MD_PHASE_PROPS, 4);
+        Phase t(s, MD_PHASE_PROPS, 3);
         GBMD_CUDA(launch_props(s->A, s->S, s->L, s->cur, true, false));
     }
     GBMD_CUDA(cudaMemcpyAsync(out, s->A.props, sizeof(md_props) * s->plan.nrep, cudaMemcpyDeviceToHost,
@@ -940,6 +964,109 @@ int md_debug_set_error(md_system* s, int32_t status)
     return MD_OK;
 }
 
+// ---- VACF / MSD measurement ----------------------------------------------------------------
+namespace {
+int dyn_shape(const md_system* s, int32_t nlag, int32_t origin_every, int32_t* norg)
+{
+    if (!s || nlag <= 0 || origin_every <= 0) return fail(MD_ERR_INVALID_ARG, "need nlag > 0 and origin_every > 0");
+    const int32_t k = (nlag + origin_every - 1) / origin_every;
+    if (k > DYN_MAX_ORG)
+        return fail(MD_ERR_INVALID_ARG, "nlag / origin_every may be at most " + std::to_string(DYN_MAX_ORG) +
+                                            " (origins followed at once)");
+    *norg = k;
+    return MD_OK;
+}
+
+size_t dyn_carve(int64_t n, int32_t nlag, char* base, DynView* V)
+{
+    Carver c{base};
+    DynView d{};
+    d.n = n;
+    d.xprev = c.take<double>(size_t(n) * 3);
+    d.v0 = c.take<double>(size_t(DYN_MAX_ORG) * n * 3);
+    d.dr = c.take<double>(size_t(DYN_MAX_ORG) * n * 3);
+    d.part = c.take<double>(size_t(DYN_BLOCKS) * 2 * DYN_MAX_ORG);
+    d.vacf = c.take<double>(size_t(nlag));
+    d.msd = c.take<double>(size_t(nlag));
+    if (V) *V = d;
+    return (c.off + 255) & ~size_t(255);
+}
+}  // namespace
+
+size_t md_dyn_workspace_bytes(const md_system* s, int32_t nlag, int32_t origin_every)
+{
+    int32_t norg = 0;
+    if (dyn_shape(s, nlag, origin_every, &norg) != MD_OK) return 0;
+    return dyn_carve(s->plan.n_total, nlag, nullptr, nullptr);
+}
+
+int md_dyn_begin(md_system* s, void* d_work, size_t work_bytes, int32_t nlag, int32_t origin_every)
+{
+    int32_t norg = 0;
+    int rc = dyn_shape(s, nlag, origin_every, &norg);
+    if (rc) return rc;
+    const size_t need = dyn_carve(s->plan.n_total, nlag, nullptr, nullptr);
+    if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u) || work_bytes < need)
+        return fail(MD_ERR_WORKSPACE, "measurement buffer missing, misaligned or smaller than " + std::to_string(need) +
+                                          " bytes");
+    dyn_carve(s->plan.n_total, nlag, static_cast<char*>(d_work), &s->dyn);
+    GBMD_CUDA(cudaMemsetAsync(s->dyn.vacf, 0, sizeof(double) * size_t(nlag), s->L.stream));
+    GBMD_CUDA(cudaMemsetAsync(s->dyn.msd, 0, sizeof(double) * size_t(nlag), s->L.stream));
+    s->dyn_on = true;
+    s->dyn_nlag = nlag;
+    s->dyn_every = origin_every;
+    s->dyn_norg = norg;
+    s->dyn_samples = 0;
+    for (int b = 0; b < DYN_MAX_ORG; ++b) s->dyn_start[b] = -1;
+    s->dyn_counts.assign(size_t(nlag), 0);
+    return MD_OK;
+}
+
+int md_dyn_sample(md_system* s)
+{
+    if (!s || !s->dyn_on) return fail(MD_ERR_INVALID_ARG, "no measurement begun (md_dyn_begin)");
+    const int64_t k = s->dyn_samples;
+    DynStep P{};
+    P.norg = s->dyn_norg;
+    P.start = -1;
+    if (k % s->dyn_every == 0) {                     // a new origin in the oldest slot
+        const int b = int((k / s->dyn_every) % s->dyn_norg);
+        s->dyn_start[b] = k;
+        P.start = b;
+    }
+    for (int b = 0; b < DYN_MAX_ORG; ++b) {
+        const int64_t lag = (b < s->dyn_norg && s->dyn_start[b] >= 0) ? k - s->dyn_start[b] : -1;
+        P.lag[b] = (lag >= 0 && lag < s->dyn_nlag) ? int(lag) : -1;
+        if (P.lag[b] >= 0) s->dyn_counts[size_t(P.lag[b])] += 1;
+    }
+    {
+        Phase t(s, MD_PHASE_OTHER, 3);
+        GBMD_CUDA(launch_forces(s->A, s->S, s->L, s->cur));
+        GBMD_CUDA(launch_dyn_sample(s->A, s->S, s->L, s->dyn, P, s->cur));
+    }
+    s->dyn_samples = k + 1;
+    return MD_OK;
+}
+
+int md_dyn_get(md_system* s, double* vacf, double* msd, int64_t* counts)
+{
+    if (!s || !s->dyn_on) return fail(MD_ERR_INVALID_ARG, "no measurement begun (md_dyn_begin)");
+    const size_t nl = size_t(s->dyn_nlag);
+    std::vector<double> a(nl), b(nl);
+    GBMD_CUDA(cudaMemcpyAsync(a.data(), s->dyn.vacf, sizeof(double) * nl, cudaMemcpyDeviceToHost, s->L.stream));
+    GBMD_CUDA(cudaMemcpyAsync(b.data(), s->dyn.msd, sizeof(double) * nl, cudaMemcpyDeviceToHost, s->L.stream));
+    const int rc = latch_error(s);
+    if (rc) return rc;
+    const double n = double(s->plan.n_total);
+    for (size_t k = 0; k < nl; ++k) {
+        const double cnt = double(s->dyn_counts[k]);
+        if (vacf) vacf[k] = cnt > 0 ? a[k] / (n * cnt) : 0.0;
+        if (msd) msd[k] = cnt > 0 ? b[k] / (n * cnt) : 0.0;
+        if (counts) counts[k] = s->dyn_counts[k];
+    }
+    return MD_OK;
+}
+
 int32_t md_nrep(const md_system* s) { return s ? s->plan.nrep : 0; }
 int64_t md_natoms(const md_system* s) { return s ? s->plan.n_total : 0; }
 int32_t md_nbr_capacity(const md_system* s) { return s ? s->plan.cap : 0; }
@@ -957,17 +1084,26 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 64) return fail(MD_ERR_INVALID_ARG, "ctas_per_sm in 0..64");
     if (t->nbr_batch && t->nbr_batch != 2 && t->nbr_batch != 4 && t->nbr_batch != 8)
         return fail(MD_ERR_INVALID_ARG, "nbr_batch must be 2, 4 or 8");
-    if (t->build_batch && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
-        return fail(MD_ERR_INVALID_ARG, "build_batch must be 2, 4 or 32");
+    if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
+        return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2, 4 or 32");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
-    if (t->step_kernel < 0 || t->step_kernel > 3) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0, 1, 2 or 3");
+    if (t->step_kernel < 0 || t->step_kernel > 4) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0..4");
+    const int old_kernel = s->L.step_kernel;
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
     if (t->build_batch) s->tune.build_batch = t->build_batch;
     if (t->use_graph) s->tune.use_graph = t->use_graph;
     if (t->step_kernel) s->tune.step_kernel = t->step_kernel;
     s->drop_graphs();          // launch shapes are baked into captured graphs
-    return apply_tuning(s);
+    int rc = apply_tuning(s);
+    if (rc) return rc;
+    if ((s->L.step_kernel == 4) != (old_kernel == 4)) {
+        // into the list-free kernel: atoms reordered by cell now; out of it: W built now
+        GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, s->L.step_kernel == 4 ? 1 : 0));
+        GBMD_CUDA(launch_rebuild(s->A, s->S, s->L, s->cur, false));
+        s->binned_fresh = false;
+    }
+    return MD_OK;
 }
 
 int md_get_tuning(const md_system* s, md_tuning* t)
@@ -1178,6 +1314,8 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
     AdjPlan P;
     int rc = adj_plan(s, nsteps, ckpt_every, &P);
     if (rc) return rc;
+    if (s->L.step_kernel == 4)
+        return fail(MD_ERR_INVALID_ARG, "the adjoint walks the neighbour matrix: select step kernel 1, 2 or 3");
     const size_t need = carve_adj(s, P, nullptr, nullptr);
     if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u) || work_bytes < need)
         return fail(MD_ERR_WORKSPACE, "adjoint workspace missing, misaligned or below " + std::to_string(need) + " bytes");

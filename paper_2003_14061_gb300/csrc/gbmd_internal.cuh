@@ -33,7 +33,7 @@ constexpr int IDX_SHIFT = 6;              // W entry: slot << 6 | (o_z+1) << 4 |
 constexpr int64_t MAX_SLOTS = int64_t(1) << 26;
 constexpr int MAX_NC = 1023;
 constexpr int SCAN_CHUNK = 2048;          // cells per block of the prefix sum
-constexpr int PROPS_SPLIT = 32;           // CTAs per replica in the first level of the final sums
+constexpr int PROPS_SPLIT_MAX = 256;      // CTAs per replica in the first level of the final sums
 constexpr int ADJ_VPART = 128;            // blocks of the |v_S|^2 partial sums
 
 enum ErrBits { ERR_NBR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
@@ -71,6 +71,8 @@ struct RepState {             // per replica, mutable on the device
     int64_t last_reorder;     // step of the last reorder
     int64_t sum_nbrs;         // sum m_i at the last rebuild
     int64_t reorders;         // reorders since creation or md_set_state
+    int32_t props_done;       // CTAs of the props reduction that have stored their slice
+    int32_t pad;
 };
 
 struct Global {               // device-wide words
@@ -100,6 +102,10 @@ struct Arrays {
     float4* xref;             // positions at the last rebuild (rule DISP)
     int32_t* perm;            // cell-ordered slots (the matrix H of Sec. 2.3, flattened)
     float4* psort;            // FP32 positions in cell order, slot in .w (MD_MIXED, MD_FP32)
+    float4* psub;             // FP32 positions sorted by half-side sub-cell, slot in .w (sub-cell build)
+    int32_t* scount;          // per sub-cell (8 per cell): occupancy, then zero again after the scan
+    int32_t* sstart;          // per sub-cell + 1: start in psub
+    int32_t* schunk;          // per SCAN_CHUNK sub-cells
     int2* tile_win;           // [ntiles][9] slot window (lo, hi) of each tile's W entries per
                               // (o_y, o_z) row, periodic-wrap entries excluded (MD_MIXED, MD_FP32)
     // reorder scratch, per slot
@@ -118,7 +124,7 @@ struct Arrays {
     int32_t* cell_rep;        // replica of every (global) cell
     int32_t* rb_base;         // per replica: its first entry in rb_tiles
     double* warp_part;        // NPROP per warp of every tile (32 slots): the props partials
-    double* slice_part;       // NPROP per (replica, slice) of the final sums
+    double* slice_part;       // NPROP per (replica, slice) of the final sums, props_split per replica
     // per replica
     Rep* rep;
     RepState* rs;
@@ -142,6 +148,9 @@ struct Scal {
     int32_t reorder_every;
     int32_t series_cap;
     int32_t shift;
+    int32_t props_split;      // CTAs per replica of the props reduction (1..PROPS_SPLIT_MAX)
+    int64_t nsub;             // half-side sub-cells (8 per cell) of the sub-cell build
+    int32_t nschunks;
     double dt, mass, c;       // c = dt / (2 m)
     double half_skin;
     double disp_margin;       // rounding margin of a displacement measured on FP32 positions
@@ -166,6 +175,25 @@ struct AdjView {
     double* lam_v;
     double* vnorm_part;       // [ADJ_VPART]
     double* out;              // [8]
+};
+
+// velocity autocorrelation / mean-square displacement measurement (md_dyn_*), in the caller's
+// buffer; per-atom arrays are indexed by permanent id
+constexpr int DYN_MAX_ORG = 8;            // time origins followed at once
+constexpr int DYN_BLOCKS = 1024;          // CTAs of the sample kernel (partial sums per CTA)
+struct DynView {
+    int64_t n;                // atoms (all replicas)
+    double* xprev;            // [n][3] wrapped positions of the previous sample
+    double* v0;               // [DYN_MAX_ORG][n][3] velocities at each origin
+    double* dr;               // [DYN_MAX_ORG][n][3] displacements since each origin
+    double* part;             // [DYN_BLOCKS][2 DYN_MAX_ORG] per-CTA sums of one sample
+    double* vacf;             // [nlag] sums over origins and atoms
+    double* msd;              // [nlag]
+};
+struct DynStep {              // one sample: which origin slot starts here, each slot's lag
+    int norg;
+    int start;                // slot whose origin is this sample (-1: none)
+    int lag[DYN_MAX_ORG];     // lag of each slot at this sample, -1 when not followed
 };
 
 // ------------------------------------------------------------------------------------------
@@ -409,7 +437,8 @@ struct Launch {
     int build_block;
     int nbr_batch;            // W entries loaded together per thread in the pair loop (2, 4, 8)
     int ctas_req;             // requested resident CTAs/SM (register bound of the step kernel)
-    int build_batch;          // candidates loaded together per thread in the build (2, 4; 32 = warp per cell)
+    int build_batch;          // candidates loaded together per thread in the build (2, 4; 32 = warp per cell;
+                              // 1 = thread per atom over half-side sub-cells)
     int step_kernel;          // 1: per-thread loads with L2 prefetch; 2: bulk-copy shared-memory ring;
                               // 3: as 1, with each tile's neighbour positions staged in shared memory
     int bulk_rows;            // rows of W staged per tile by the ring (step_kernel 2)
@@ -437,6 +466,7 @@ cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, in
 cudaError_t launch_reorder(const Arrays& A, const Scal& S, const Launch& L, int cur);                    // 2 kernels
 cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur);                // 3 kernels
 constexpr int REBUILD_KERNELS = 12;       // kernels of one rebuild sequence (bin/order 7, reorder 2, build 3)
+int build_kernels(const Scal& S, const Launch& L);   // kernels of launch_build_only (2, 3 or 9)
 
 // adjoint (kernels_adjoint.cu)
 cudaError_t launch_adj_reverse(const Arrays& A, const Scal& S, const Launch& L, const AdjView& V, int q, double kappa,
@@ -446,6 +476,10 @@ cudaError_t launch_adj_permute(const Arrays& A, const Scal& S, const Launch& L, 
                                double kappa);
 cudaError_t launch_adj_init(const AdjView& V, const Launch& L, int64_t n, const double* vS);
 cudaError_t launch_adj_final(const AdjView& V, const Launch& L, int ntiles);
+
+// measurement (kernels_dyn.cu): one VACF / MSD sample (the forces must be current)
+cudaError_t launch_dyn_sample(const Arrays& A, const Scal& S, const Launch& L, const DynView& D, const DynStep& P,
+                              int cur);
 
 // step path (kernels_step.cu)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props);

@@ -280,7 +280,18 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* sh_warp, int& to
     return r;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(Arrays A, Scal S)
+// The scan of n counters `count` into `start` (n + 1 entries), through per-chunk totals in
+// `chunk`; the counters are left at zero for the next binning.  Serves the cells and the half-side
+// sub-cells of the sub-cell neighbour build.
+struct ScanArgs {
+    int32_t* count;
+    int32_t* start;
+    int32_t* chunk;
+    int64_t n;
+    int32_t nchunks;
+};
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(Arrays A, ScanArgs C)
 {
     if (!A.g->any_rebuild) return;
     __shared__ int sh[33];
@@ -289,29 +300,29 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_chunks(Arrays A, Scal S)
 #pragma unroll
     for (int k = 0; k < SCAN_PER_THREAD; ++k) {
         const int64_t c = base + k;
-        if (c < S.ncells) s += A.ccount[c];
+        if (c < C.n) s += C.count[c];
     }
     int total;
     block_exclusive_scan(s, sh, total);
-    if (threadIdx.x == 0) A.chunk[blockIdx.x] = total;
+    if (threadIdx.x == 0) C.chunk[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_top(Arrays A, Scal S)
+__global__ void __launch_bounds__(1024) k_scan_top(Arrays A, ScanArgs C)
 {
     if (!A.g->any_rebuild) return;
     __shared__ int sh[33];
     int carry = 0;
-    for (int b0 = 0; b0 < S.nchunks; b0 += blockDim.x) {
+    for (int b0 = 0; b0 < C.nchunks; b0 += blockDim.x) {
         const int b = b0 + threadIdx.x;
-        const int v = (b < S.nchunks) ? A.chunk[b] : 0;
+        const int v = (b < C.nchunks) ? C.chunk[b] : 0;
         int total;
         const int ex = block_exclusive_scan(v, sh, total);
-        if (b < S.nchunks) A.chunk[b] = carry + ex;
+        if (b < C.nchunks) C.chunk[b] = carry + ex;
         carry += total;
     }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(Arrays A, Scal S)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(Arrays A, ScanArgs C)
 {
     if (!A.g->any_rebuild) return;
     __shared__ int sh[33];
@@ -321,21 +332,28 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(Arrays A, Scal S)
 #pragma unroll
     for (int k = 0; k < SCAN_PER_THREAD; ++k) {
         const int64_t c = base + k;
-        v[k] = (c < S.ncells) ? A.ccount[c] : 0;
+        v[k] = (c < C.n) ? C.count[c] : 0;
         s += v[k];
     }
     int total;
-    int run = A.chunk[blockIdx.x] + block_exclusive_scan(s, sh, total);
+    int run = C.chunk[blockIdx.x] + block_exclusive_scan(s, sh, total);
 #pragma unroll
     for (int k = 0; k < SCAN_PER_THREAD; ++k) {
         const int64_t c = base + k;
-        if (c < S.ncells) {
-            A.cstart[c] = run;
-            A.ccount[c] = 0;              // ready for the next binning
+        if (c < C.n) {
+            C.start[c] = run;
+            C.count[c] = 0;               // ready for the next binning
             run += v[k];
-            if (c == S.ncells - 1) A.cstart[S.ncells] = run;
+            if (c == C.n - 1) C.start[C.n] = run;
         }
     }
+}
+
+static void launch_scan(const Arrays& A, const ScanArgs& C, cudaStream_t st)
+{
+    k_scan_chunks<<<C.nchunks, SCAN_THREADS, 0, st>>>(A, C);
+    k_scan_top<<<1, 1024, 0, st>>>(A, C);
+    k_scan_apply<<<C.nchunks, SCAN_THREADS, 0, st>>>(A, C);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -742,6 +760,216 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
 }
 
 // ------------------------------------------------------------------------------------------
+// N5 over half-side sub-cells.  Every cell of side w >= r_c + skin is split into 2 x 2 x 2
+// sub-cells of side w / 2 (an atom's sub-cell along an axis is 2 c + (l >= w / 2)), and the atoms
+// are counting-sorted by sub-cell into psub (rows of sub-cells along x contiguous, ascending slot
+// within a sub-cell).  A neighbour lies at most 2 sub-cells away along each axis, and of the
+// 5 x 5 x 5 sub-cells around an atom only those whose nearest point is within r_c + skin are
+// scanned: a row (fixed y, z) at a time, as one contiguous run of psub.  That tests about half
+// the candidates of the 27 cells (WCA) and 40 % of them at the LJ cutoff.  The test itself is
+// the criterion's expression, d = (lf_j - lf_i) + o * wf with o the offset of j's cell, so the
+// sets are those of k_build_sorted (the order within a column follows the sub-cell rows).
+// The sub-cell slot of an atom is kept in A.layer (free once the cell order is built).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int sub_of(float l, float w, int c) { return 2 * c + ((l >= 0.5f * w) ? 1 : 0); }
+
+__device__ __forceinline__ int64_t sub_index(const Rep& R, int sx, int sy, int sz)
+{
+    return int64_t(8) * R.cell0 + (int64_t(sz) * (2 * R.nc[1]) + sy) * (2 * R.nc[0]) + sx;
+}
+
+__device__ __forceinline__ int64_t sub_of_atom(const Rep& R, const float4& p)
+{
+    int cx, cy, cz;
+    unpack_cell(__float_as_uint(p.w), cx, cy, cz);
+    return sub_index(R, sub_of(p.x, R.wf[0], cx), sub_of(p.y, R.wf[1], cy), sub_of(p.z, R.wf[2], cz));
+}
+
+__global__ void __launch_bounds__(TILE) k_sub_bin(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_rebuild) return;
+    const int nrb = A.g->n_rb_tiles;
+    for (int it = blockIdx.x; it < nrb; it += gridDim.x) {
+        const int t = A.rb_tiles[it];
+        const Rep& R = A.rep[A.tile_rep[t]];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const bool active = slot - R.slot0 < R.n;
+        const long long sub = active ? sub_of_atom(R, A.pos32[cur][slot]) : -1;
+        // lanes of a warp that share a sub-cell take consecutive slots from one atomic
+        const unsigned peers = __match_any_sync(0xffffffffu, sub);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int base = 0;
+        if (active && lane == leader) base = atomicAdd(&A.scount[sub], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (active) A.layer[slot] = base + rank;
+    }
+}
+
+__global__ void __launch_bounds__(TILE) k_sub_scatter(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_rebuild) return;
+    const int nrb = A.g->n_rb_tiles;
+    for (int it = blockIdx.x; it < nrb; it += gridDim.x) {
+        const int t = A.rb_tiles[it];
+        const Rep& R = A.rep[A.tile_rep[t]];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        if (slot - R.slot0 >= R.n) continue;
+        const float4 p = A.pos32[cur][slot];
+        A.psub[A.sstart[sub_of_atom(R, p)] + A.layer[slot]] = make_float4(p.x, p.y, p.z, __int_as_float(int(slot)));
+    }
+}
+
+// ascending slot within each sub-cell (the atomic slots leave the order to chance)
+__global__ void __launch_bounds__(256) k_sub_sort(Arrays A, Scal S)
+{
+    if (!A.g->any_rebuild) return;
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < S.nsub; c += int64_t(gridDim.x) * blockDim.x) {
+        const int b = A.sstart[c], e = A.sstart[c + 1];
+        for (int k = b + 1; k < e; ++k) {
+            const float4 key = A.psub[k];
+            int q = k - 1;
+            while (q >= b && __float_as_int(A.psub[q].w) > __float_as_int(key.w)) {
+                A.psub[q + 1] = A.psub[q];
+                --q;
+            }
+            A.psub[q + 1] = key;
+        }
+    }
+}
+
+// squared distance from l to the sub-cell interval [j h, (j + 1) h) of the atom's cell frame
+__device__ __forceinline__ float sub_gap2(float l, int j, float h)
+{
+    const float lo = float(j) * h, hi = lo + h;
+    const float d = (l < lo) ? lo - l : ((l > hi) ? l - hi : 0.0f);
+    return d * d;
+}
+
+template <int BB>
+__global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
+{
+    if (!A.g->any_rebuild) return;
+    const float4* __restrict__ pos = A.pos32[cur];
+    const float4* __restrict__ ps = A.psub;
+    const int32_t* __restrict__ ss = A.sstart;
+    const float rl2 = S.rl2f;
+    const float skip2 = rl2 * (1.0f + 1e-5f);
+    const int nrb = A.g->n_rb_tiles;
+    const int per = (nrb + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(nrb, t_begin + per);
+    int run_r = -1, run_max = 0;
+    long long run_sum = 0;
+    for (int it = t_begin; it < t_end; ++it) {
+        const int t = A.rb_tiles[it];
+        const int r = A.tile_rep[t];
+        if (r != run_r) {
+            if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
+            run_r = r;
+            run_sum = 0;
+            run_max = 0;
+        }
+        const Rep& R = A.rep[r];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        const bool active = slot - R.slot0 < R.n;
+        int m = 0;
+        if (active) {
+            const float4 pi = pos[slot];
+            int cx, cy, cz;
+            unpack_cell(__float_as_uint(pi.w), cx, cy, cz);
+            const float w0 = R.wf[0], w1 = R.wf[1], w2 = R.wf[2];
+            const float h0 = 0.5f * w0, h1 = 0.5f * w1, h2 = 0.5f * w2;
+            // the atom's half along each axis; sub-cell j = b + d (d = -2..2) of the cell frame
+            const int bx = (pi.x >= h0) ? 1 : 0, by = (pi.y >= h1) ? 1 : 0, bz = (pi.z >= h2) ? 1 : 0;
+            const int nsx = 2 * R.nc[0], nsy = 2 * R.nc[1], nsz = 2 * R.nc[2];
+            float gx[5];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) gx[d] = sub_gap2(pi.x, bx + d - 2, h0);
+            const int me = int(slot);
+            uint32_t* wp = A.W + slot;
+            const float2 npxy = make_float2(-pi.x, -pi.y);
+            const float npz = -pi.z;
+            for (int dz = 0; dz < 5; ++dz) {
+                const int jz = bz + dz - 2;
+                const float gz = sub_gap2(pi.z, jz, h2);
+                if (gz > skip2) continue;
+                const int oz = jz >> 1;                            // offset of the sub-cell's cell
+                int sz = 2 * cz + jz; sz += (sz < 0) ? nsz : 0; sz -= (sz >= nsz) ? nsz : 0;
+                const float offz = float(oz) * w2;
+                for (int dy = 0; dy < 5; ++dy) {
+                    const int jy = by + dy - 2;
+                    const float gyz = sub_gap2(pi.y, jy, h1) + gz;
+                    if (gyz > skip2) continue;
+                    // the sub-cells of this row within reach form one range d = lo .. hi
+                    int lo = 5, hi = -1;
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+                        if (gyz + gx[d] <= skip2) {
+                            lo = min(lo, d);
+                            hi = d;
+                        }
+                    }
+                    if (hi < 0) continue;
+                    const int oy = jy >> 1;
+                    int sy = 2 * cy + jy; sy += (sy < 0) ? nsy : 0; sy -= (sy >= nsy) ? nsy : 0;
+                    const float offy = float(oy) * w1;
+                    const uint32_t codeyz = (uint32_t(oy + 1) << 2) | (uint32_t(oz + 1) << 4);
+                    const int64_t row = sub_index(R, 0, sy, sz);
+                    const int sxl = 2 * cx + bx + lo - 2, sxh = 2 * cx + bx + hi - 2;
+                    if (sxl >= 0 && sxh < nsx) {
+                        // one run of psub; the cells change at sub-cells 2 cx and 2 cx + 2
+                        const int kb = ss[row + sxl], ke = ss[row + sxh + 1];
+                        const int b1 = ss[row + min(max(2 * cx, sxl), sxh + 1)];
+                        const int b2 = ss[row + min(max(2 * cx + 2, sxl), sxh + 1)];
+                        for (int k0 = kb; k0 < ke; k0 += BB) {
+                            float4 pj[BB];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) pj[u] = ps[min(k0 + u, ke - 1)];
+#pragma unroll
+                            for (int u = 0; u < BB; ++u) {
+                                const int k = k0 + u;
+                                const uint32_t c = uint32_t(k >= b1) + uint32_t(k >= b2);   // o_x + 1
+                                const float offx = (k < b1) ? -w0 : ((k < b2) ? 0.0f : w0);
+                                nbr_test(pj[u], npxy, npz, offx, offy, offz, k < ke, codeyz | c, me, rl2, wp, m,
+                                         S.cap, S.nslots);
+                            }
+                        }
+                    } else {
+                        // a periodic wrap in x: sub-cell by sub-cell
+                        for (int d = lo; d <= hi; ++d) {
+                            const int jx = bx + d - 2;
+                            const int ox = jx >> 1;
+                            int sx = 2 * cx + jx; sx += (sx < 0) ? nsx : 0; sx -= (sx >= nsx) ? nsx : 0;
+                            const int b = ss[row + sx], e = ss[row + sx + 1];
+                            const float offx = float(ox) * w0;
+                            for (int k0 = b; k0 < e; k0 += BB) {
+                                float4 pj[BB];
+#pragma unroll
+                                for (int u = 0; u < BB; ++u) pj[u] = ps[min(k0 + u, e - 1)];
+#pragma unroll
+                                for (int u = 0; u < BB; ++u)
+                                    nbr_test(pj[u], npxy, npz, offx, offy, offz, k0 + u < e, codeyz | uint32_t(ox + 1), me,
+                                             rl2, wp, m, S.cap, S.nslots);
+                            }
+                        }
+                    }
+                }
+            }
+            A.nbr_count[slot] = m;
+            if (S.rule == MD_REBUILD_DISP) A.xref[slot] = make_float4(pi.x, pi.y, pi.z, 0.0f);
+            if (m > S.cap) {
+                atomicOr(&A.g->err, ERR_NBR_OVERFLOW);
+                atomicMax(&A.g->max_nbr_seen, m);
+            }
+            run_sum += m;
+            run_max = max(run_max, m);
+        }
+    }
+    if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
+}
+
+// ------------------------------------------------------------------------------------------
 // N5 for dense cells (tens of atoms per cell, e.g. the LJ liquid at r_c + skin = 2.8): one warp
 // per cell, one lane per atom of it.  The candidates of each 3-cell row of the 27-cell
 // neighbourhood are staged once in the warp's shared memory (coalesced loads, double-buffered:
@@ -1081,6 +1309,9 @@ void prime_rebuild_grids(const Scal& S, const Launch& L)
     (void)resident_grid<k_scatter>(S, L);
     (void)resident_grid<k_build_sorted<2>>(S, L);
     (void)resident_grid<k_build_sorted<4>>(S, L);
+    (void)resident_grid<k_build_sub<2>>(S, L);
+    (void)resident_grid<k_sub_bin>(S, L);
+    (void)resident_grid<k_sub_scatter>(S, L);
     (void)resident_grid<k_reorder_gather<MD_FP64>>(S, L);
     (void)resident_grid<k_reorder_gather<MD_MIXED>>(S, L);
     (void)resident_grid<k_reorder_gather<MD_FP32>>(S, L);
@@ -1102,9 +1333,7 @@ cudaError_t launch_bin_order(const Arrays& A, const Scal& S, const Launch& L, in
     if (S.mode == MD_FP64) k_bin<MD_FP64><<<resident_grid<k_bin<MD_FP64>>(S, L), TILE, 0, L.stream>>>(A, S, cur, fs);
     else if (S.mode == MD_MIXED) k_bin<MD_MIXED><<<resident_grid<k_bin<MD_MIXED>>(S, L), TILE, 0, L.stream>>>(A, S, cur, fs);
     else k_bin<MD_FP32><<<resident_grid<k_bin<MD_FP32>>(S, L), TILE, 0, L.stream>>>(A, S, cur, fs);
-    k_scan_chunks<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
-    k_scan_top<<<1, 1024, 0, L.stream>>>(A, S);
-    k_scan_apply<<<S.nchunks, SCAN_THREADS, 0, L.stream>>>(A, S);
+    launch_scan(A, ScanArgs{A.ccount, A.cstart, A.chunk, S.ncells, S.nchunks}, L.stream);
     k_scatter<<<resident_grid<k_scatter>(S, L), TILE, 0, L.stream>>>(A, S);
     const int gs = int(std::min<int64_t>((S.ncells + 255) / 256, int64_t(L.grid) * 8));
     k_sort_cells<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S, cur);
@@ -1132,10 +1361,25 @@ cudaError_t launch_bin_only(const Arrays& A, const Scal& S, const Launch& L, int
     return launch_reorder(A, S, L, cur);
 }
 
+// the list-free step kernel reads no neighbour matrix; it is built only where the exact
+// displacement rule needs the positions at the rebuild (written by the build)
+static bool skip_w(const Scal& S, const Launch& L) { return L.step_kernel == 4 && S.rule != MD_REBUILD_DISP; }
+
+int build_kernels(const Scal& S, const Launch& L) { return skip_w(S, L) ? 2 : (L.build_batch == 1 ? 9 : 3); }
+
 cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur)
 {
     const int g = tile_grid(S, L);
     if (S.mode == MD_FP64) k_build<double, 1><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (skip_w(S, L)) {
+    } else if (L.build_batch == 1) {
+        k_sub_bin<<<resident_grid<k_sub_bin>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+        launch_scan(A, ScanArgs{A.scount, A.sstart, A.schunk, S.nsub, S.nschunks}, L.stream);
+        k_sub_scatter<<<resident_grid<k_sub_scatter>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+        const int gs = int(std::min<int64_t>((S.nsub + 255) / 256, int64_t(L.grid) * 8));
+        k_sub_sort<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S);
+        k_build_sub<2><<<resident_grid<k_build_sub<2>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+    }
     else if (L.build_batch >= 32) k_build_cw<<<std::max(1, L.grid), TILE, 0, L.stream>>>(A, S, cur);
     else if (L.build_batch >= 4) k_build_sorted<4><<<resident_grid<k_build_sorted<4>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
     else k_build_sorted<2><<<resident_grid<k_build_sorted<2>>(S, L), TILE, 0, L.stream>>>(A, S, cur);

@@ -131,6 +131,86 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
     return force_f32_rows<NB>(A, S, R, pos, slot, pi, min(__ldcs(A.nbr_count + slot), S.cap));
 }
 
+// Two pairs (lanes x and y) of the FP32 pair loop: g(r^2) with the in-range masks, accumulated
+// into f (sum g (x_j - x_i)), u_i and the virial.
+__device__ __forceinline__ void pair2(const Scal& S, float2 dx, float2 dy, float2 dz, bool in0, bool in1,
+                                      float2& fx, float2& fy, float2& fz, float2& u, float2& w)
+{
+    const float2 sig2 = make_float2(S.sig2f, S.sig2f), eps48 = make_float2(S.eps48f, S.eps48f);
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    in0 = in0 && r2.x < S.rc2f;
+    in1 = in1 && r2.y < S.rc2f;
+    const float2 ri2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    const float2 sr2 = __fmul2_rn(sig2, ri2);
+    const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
+    float2 fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(eps48, sr6), __fadd2_rn(sr6, make_float2(-0.5f, -0.5f))), ri2);
+    fs.x = in0 ? fs.x : 0.0f;
+    fs.y = in1 ? fs.y : 0.0f;
+    fx = __ffma2_rn(fs, dx, fx);
+    fy = __ffma2_rn(fs, dy, fy);
+    fz = __ffma2_rn(fs, dz, fz);
+    float2 ut = __ffma2_rn(__fmul2_rn(make_float2(S.eps4f, S.eps4f), sr6), __fadd2_rn(sr6, make_float2(-1.0f, -1.0f)),
+                           make_float2(-S.ucf, -S.ucf));
+    ut.x = in0 ? ut.x : 0.0f;
+    ut.y = in1 ? ut.y : 0.0f;
+    u = __fadd2_rn(u, ut);
+    w = __ffma2_rn(fs, r2, w);
+}
+
+// F1 without a neighbour matrix (step kernel 4, the cell-block alternative of Sec. 4.2 item 1).
+// The atoms are in cell order (reordered at every rebuild), so the 3 cells of each row around the
+// atom are one contiguous run of slots; every atom of the 27 cells is tested against r_c at the
+// current positions.  The cells, of side >= r_c + skin, were binned at the last rebuild and no
+// atom has moved more than skin/2 since, so no pair within r_c is missed.  Two candidates at a
+// time go through the packed pair arithmetic; the offset of a candidate's cell is o w, as in
+// the neighbour-matrix loop.
+__device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, const Rep& R,
+                                                const float4* __restrict__ pos, int64_t slot, float4 pi)
+{
+    int cx, cy, cz;
+    unpack_cell(__float_as_uint(pi.w), cx, cy, cz);
+    const int32_t* __restrict__ cs = A.cstart;
+    const int64_t sbase = R.slot0 - cs[R.cell0];            // slot of cell-order position k
+    const int ncx = R.nc[0];
+    const float wx = R.wf[0];
+    const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
+    float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, u = fx, w = fx;
+    const int xs[3] = {(cx == 0) ? ncx - 1 : cx - 1, cx, (cx == ncx - 1) ? 0 : cx + 1};
+    const bool inner = cx > 0 && cx < ncx - 1;
+    for (int oz = -1; oz <= 1; ++oz) {
+        int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
+        const float2 offz = make_float2(float(oz) * R.wf[2], float(oz) * R.wf[2]);
+        for (int oy = -1; oy <= 1; ++oy) {
+            int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
+            const float2 offy = make_float2(float(oy) * R.wf[1], float(oy) * R.wf[1]);
+            const int row = R.cell0 + row_pos(R, ny, nz) * ncx;
+            // runs [b, e) with their x offsets: one run of three cells, or three at a wrap in x
+            const int nrun = inner ? 1 : 3;
+            for (int q = 0; q < nrun; ++q) {
+                const int b = inner ? cs[row + cx - 1] : cs[row + xs[q]];
+                const int e = inner ? cs[row + cx + 2] : cs[row + xs[q] + 1];
+                const int b1 = inner ? cs[row + cx] : e, b2 = inner ? cs[row + cx + 1] : e;
+                const float oq = inner ? -1.0f : float(q - 1);
+                for (int k0 = b; k0 < e; k0 += 2) {
+                    const int k1 = k0 + 1;
+                    const bool v1 = k1 < e;
+                    const int64_t j0 = sbase + k0, j1 = sbase + (v1 ? k1 : k0);
+                    const float4 p0 = __ldg(pos + j0), p1 = __ldg(pos + j1);
+                    // o_x of each candidate: the run's first cell, +1 past b1, +2 past b2
+                    const float o0 = oq + float(k0 >= b1) + float(k0 >= b2);
+                    const float o1 = oq + float(k1 >= b1) + float(k1 >= b2);
+                    const float2 dx = __ffma2_rn(make_float2(o0, o1), make_float2(wx, wx),
+                                                 __fadd2_rn(make_float2(p0.x, p1.x), npx));
+                    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(p0.y, p1.y), npy), offy);
+                    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(p0.z, p1.z), npz), offz);
+                    pair2(S, dx, dy, dz, j0 != slot, v1 && j1 != slot, fx, fy, fz, u, w);
+                }
+            }
+        }
+    }
+    return AccF{-(fx.x + fx.y), -(fy.x + fy.y), -(fz.x + fz.y), u.x + u.y, w.x + w.y};
+}
+
 // Leapfrog kick and drift of one atom (Sec. 4.3 item 1) from its force a: MD_MIXED advances the
 // FP64 state (v, x), MD_FP32 the FP32 velocity v32 and position pi; pn receives the FP32
 // cell-local position of step n+1.  FP32<->FP64 conversions run on the integer pipe (bit for bit
@@ -621,7 +701,7 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
     __syncwarp();
 }
 
-template <int MODE, bool PROPS, int NB, int MINB>
+template <int MODE, bool PROPS, int NB, int MINB, bool CELLS = false>
 __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                       int use_cond)
 {
@@ -676,7 +756,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
     // L2 and the claim of the one after it is in flight
     int w0 = claim_now();
     int w1 = (w0 >= 0) ? claim_now() : -1;
-    int c0 = (w0 >= 0) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
+    int c0 = (w0 >= 0 && !CELLS) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
     int run_r = -1, run_cnt = 0;
     float run_max = 0.0f;
     while (w0 >= 0) {
@@ -703,7 +783,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
                 }
                 prefetch_l2(p);
             }
-            c1 = __ldcs(A.nbr_count + s1 + lane);
+            if (!CELLS) c1 = __ldcs(A.nbr_count + s1 + lane);
         }
         const int t = w0 / (TILE / 32);
         const int r = A.tile_rep[t];
@@ -723,7 +803,8 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         for (int q = 0; q < NPROP; ++q) part[q] = 0.0f;
         if (active) {
             const float4 pi = __ldg(pos + slot);
-            const AccF a = force_f32_rows<NB>(A, S, R, pos, slot, pi, min(c0, S.cap));
+            const AccF a = CELLS ? force_f32_cells(A, S, R, pos, slot, pi)
+                                 : force_f32_rows<NB>(A, S, R, pos, slot, pi, min(c0, S.cap));
             double v[3], x[3];
             float v32[3], pn[3];
 #pragma unroll
@@ -760,7 +841,8 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         if (w1 >= 0) {
             // the rows of W below the next warp-tile's largest count into L2
             const int mw = min(__reduce_max_sync(0xffffffffu, unsigned(c1)), unsigned(S.cap));
-            for (int k = lane; k < mw; k += 32) prefetch_l2(A.W + int64_t(k) * S.nslots + int64_t(w1) * 32);
+            if (!CELLS)
+                for (int k = lane; k < mw; k += 32) prefetch_l2(A.W + int64_t(k) * S.nslots + int64_t(w1) * 32);
             if (pending) {
                 const int k = __shfl_sync(0xffffffffu, pend, 0);
                 if (k < range_len(home)) w2 = home * per + k;
@@ -945,7 +1027,7 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
 // ------------------------------------------------------------------------------------------
 // forces only (F1): f, u_i, per-atom virial
 // ------------------------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, bool CELLS = false>
 __global__ void __launch_bounds__(TILE) k_forces(Arrays A, Scal S, int cur)
 {
     for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
@@ -960,7 +1042,8 @@ __global__ void __launch_bounds__(TILE) k_forces(Arrays A, Scal S, int cur)
             A.wvir[slot] = a.w;
         } else {
             const float4 pi = A.pos32[cur][slot];
-            const AccF a = force_f32<4>(A, S, R, A.pos32[cur], slot, pi);
+            const AccF a = CELLS ? force_f32_cells(A, S, R, A.pos32[cur], slot, pi)
+                                 : force_f32<4>(A, S, R, A.pos32[cur], slot, pi);
             A.f[slot] = make_double4_32a(a.fx, a.fy, a.fz, a.u);
             A.wvir[slot] = a.w;
         }
@@ -1000,59 +1083,73 @@ __global__ void __launch_bounds__(TILE) k_props_tiles(Arrays A, Scal S)
     }
 }
 
-// Final sums, in a fixed order: PROPS_SPLIT CTAs per replica each add a contiguous slice of the
-// replica's tiles (each tile the sum of its warps' partials in warp order), then one warp per
-// replica adds the slices and applies the constant factors (U = sum u_i / 2, K = m sum v^2 / 2,
-// W = sum w_i / 2, P = m sum v).
-__global__ void __launch_bounds__(256) k_props_slices(Arrays A, Scal S)
+// Final sums, in a fixed order, in one launch: S.props_split CTAs per replica each add a
+// contiguous slice of the replica's warp partials (thread t the rows t, t + 128, ...; then a
+// tree over the threads in shared memory), store the slice's sums, and count themselves in; the
+// CTA that completes the replica (the last-block pattern of Sec. 2.3's reductions: a fence,
+// then an atomic counter) adds the slices the same way and writes the props, applying the
+// constant factors (U = sum u_i / 2, K = m sum v^2 / 2, W = sum w_i / 2, P = m sum v), and the
+// time-series row.
+constexpr int PROPS_THREADS = 128;
+
+__device__ __forceinline__ void props_tree(double (*sh)[NPROP], double (&acc)[NPROP])
 {
-    __shared__ double sh[256][NPROP];
-    const int r = blockIdx.x / PROPS_SPLIT, b = blockIdx.x % PROPS_SPLIT;
-    const Rep& R = A.rep[r];
-    const int per = (R.ntiles + PROPS_SPLIT - 1) / PROPS_SPLIT;
-    const int k0 = b * per, k1 = min(R.ntiles, k0 + per);
-    double acc[NPROP];
-#pragma unroll
-    for (int q = 0; q < NPROP; ++q) acc[q] = 0.0;
-    for (int k = k0 + int(threadIdx.x); k < k1; k += blockDim.x) {
-        const double* w = A.warp_part + int64_t(R.tile0 + k) * (TILE / 32) * NPROP;
-#pragma unroll
-        for (int q = 0; q < NPROP; ++q) {
-            double y = w[q];
-#pragma unroll
-            for (int j = 1; j < TILE / 32; ++j) y = (q == NPROP - 1) ? fmax(y, w[j * NPROP + q]) : y + w[j * NPROP + q];
-            acc[q] = (q == NPROP - 1) ? fmax(acc[q], y) : acc[q] + y;
-        }
-    }
 #pragma unroll
     for (int q = 0; q < NPROP; ++q) sh[threadIdx.x][q] = acc[q];
     __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
+    for (int h = PROPS_THREADS / 2; h > 0; h >>= 1) {
+        if (int(threadIdx.x) < h) {
 #pragma unroll
             for (int q = 0; q < NPROP - 1; ++q) sh[threadIdx.x][q] += sh[threadIdx.x + h][q];
             sh[threadIdx.x][NPROP - 1] = fmax(sh[threadIdx.x][NPROP - 1], sh[threadIdx.x + h][NPROP - 1]);
         }
         __syncthreads();
     }
-    if (threadIdx.x < NPROP) A.slice_part[int64_t(blockIdx.x) * NPROP + threadIdx.x] = sh[0][threadIdx.x];
 }
 
-__global__ void __launch_bounds__(32) k_props_finalize(Arrays A, Scal S, int to_series, int step_lag)
+__global__ void __launch_bounds__(PROPS_THREADS) k_props_reduce(Arrays A, Scal S, int to_series, int step_lag)
 {
-    const int r = blockIdx.x;
+    __shared__ double sh[PROPS_THREADS][NPROP];
+    __shared__ int sh_last;
+    const int split = S.props_split;
+    const int r = blockIdx.x / split, b = blockIdx.x % split;
     const Rep& R = A.rep[r];
-    if (threadIdx.x != 0) return;
+    const int64_t rows = int64_t(R.ntiles) * (TILE / 32);            // warp partials of the replica
+    const int64_t per = (rows + split - 1) / split;
+    const int64_t w0 = int64_t(R.tile0) * (TILE / 32) + b * per;
+    const int64_t w1 = int64_t(R.tile0) * (TILE / 32) + min(rows, (b + 1) * per);
     double acc[NPROP];
 #pragma unroll
     for (int q = 0; q < NPROP; ++q) acc[q] = 0.0;
-    for (int b = 0; b < PROPS_SPLIT; ++b) {
-        const double* p = A.slice_part + (int64_t(r) * PROPS_SPLIT + b) * NPROP;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += PROPS_THREADS) {
+        const double* p = A.warp_part + w * NPROP;
 #pragma unroll
         for (int q = 0; q < NPROP - 1; ++q) acc[q] += p[q];
         acc[NPROP - 1] = fmax(acc[NPROP - 1], p[NPROP - 1]);
     }
-    const RepState& st = A.rs[r];
+    props_tree(sh, acc);
+    if (threadIdx.x < NPROP) A.slice_part[int64_t(blockIdx.x) * NPROP + threadIdx.x] = sh[0][threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(&A.rs[r].props_done, 1) == split - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NPROP; ++q) acc[q] = 0.0;
+    for (int k = threadIdx.x; k < split; k += PROPS_THREADS) {
+        const double* p = A.slice_part + (int64_t(r) * split + k) * NPROP;
+#pragma unroll
+        for (int q = 0; q < NPROP - 1; ++q) acc[q] += __ldcg(p + q);
+        acc[NPROP - 1] = fmax(acc[NPROP - 1], __ldcg(p + NPROP - 1));
+    }
+    __syncthreads();
+    props_tree(sh, acc);
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int q = 0; q < NPROP; ++q) acc[q] = sh[0][q];
+    RepState& st = A.rs[r];
+    st.props_done = 0;                               // ready for the next reduction
     const double U = 0.5 * acc[0], K = 0.5 * S.mass * acc[1], W = 0.5 * acc[2];
     const double V = R.L[0] * R.L[1] * R.L[2];
     md_props pr;
@@ -1071,14 +1168,13 @@ __global__ void __launch_bounds__(32) k_props_finalize(Arrays A, Scal S, int to_
     pr.reorders = st.reorders;
     A.props[r] = pr;
     if (to_series) {
-        RepState& sw = A.rs[r];
         // ring of series_cap rows laid out [row][replica][column]: the latest row of every
         // replica is contiguous (one copy reads it)
-        const int row = sw.series_rows % S.series_cap;
+        const int row = st.series_rows % S.series_cap;
         double* o = A.series + (int64_t(row) * S.nrep + r) * SERIES_COLS;
         o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
         o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
-        sw.series_rows += 1;
+        st.series_rows += 1;
     }
 }
 
@@ -1098,6 +1194,7 @@ __global__ void __launch_bounds__(TILE) k_set_state(Arrays A, Scal S, int cur)
             st.D = 0.0; st.vmax2 = 0u; st.rebuild = 0; st.reorder = 0; st.vhalf = 0;
             st.tiles_done = 0; st.max_nbrs = 0; st.max_occ = 0; st.series_rows = 0;
             st.step = 0; st.rebuilds = 0; st.last_reorder = 0; st.sum_nbrs = 0; st.reorders = 0;
+            st.props_done = 0;
         }
         if (j >= R.n) continue;
         const int64_t id = R.id0 + j;
@@ -1294,10 +1391,26 @@ void stage_shape(int ctas_per_sm, int smem_per_sm, int* cap, int* smem_bytes)
     *smem_bytes = c * 16;
 }
 
+template <int M, int MINB>
+static int occ_cells()
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, false, 2, MINB, true>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_sm<M, true, 2, MINB, true>, TILE, 0);
+    return std::max(1, std::min(a, b));
+}
+
 int step_ctas_per_sm(const Scal& S, const Launch& L)
 {
     int occ = 1;
     if (S.mode == MD_FP64) return occ_of<MD_FP64, 2, 4>();
+    if (L.step_kernel == 4) {
+        const int mb = minb_of(L.ctas_req);
+        if (S.mode == MD_MIXED) return mb == 16 ? occ_cells<MD_MIXED, 16>() : mb == 12 ? occ_cells<MD_MIXED, 12>()
+                                       : mb == 8 ? occ_cells<MD_MIXED, 8>() : occ_cells<MD_MIXED, 4>();
+        return mb == 16 ? occ_cells<MD_FP32, 16>() : mb == 12 ? occ_cells<MD_FP32, 12>()
+               : mb == 8 ? occ_cells<MD_FP32, 8>() : occ_cells<MD_FP32, 4>();
+    }
     if (L.step_kernel == 3) {
 #define GBMD_OCC(M, NB, MB) { occ = occ_staged<M, NB, MB>(L.stage_smem); }
         if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_OCC)
@@ -1331,6 +1444,22 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
         if (S.mode == MD_MIXED) GBMD_DISPATCH_NB(MD_MIXED, GBMD_STEP_BULK)
         else GBMD_DISPATCH_NB(MD_FP32, GBMD_STEP_BULK)
 #undef GBMD_STEP_BULK
+    } else if (S.mode != MD_FP64 && L.step_kernel == 4) {
+#define GBMD_STEP_CELLS(M, MB)                                                                              \
+    {                                                                                                       \
+        if (props) k_step_sm<M, true, 2, MB, true><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);   \
+        else k_step_sm<M, false, 2, MB, true><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);        \
+    }
+#define GBMD_CELLS_MB(M)                                                                                    \
+    {                                                                                                       \
+        const int mb = minb_of(L.ctas_req);                                                                 \
+        if (mb == 16) GBMD_STEP_CELLS(M, 16) else if (mb == 12) GBMD_STEP_CELLS(M, 12)                      \
+        else if (mb == 8) GBMD_STEP_CELLS(M, 8) else GBMD_STEP_CELLS(M, 4)                                  \
+    }
+        if (S.mode == MD_MIXED) GBMD_CELLS_MB(MD_MIXED)
+        else GBMD_CELLS_MB(MD_FP32)
+#undef GBMD_CELLS_MB
+#undef GBMD_STEP_CELLS
     } else if (S.mode != MD_FP64 && L.step_kernel == 3) {
 #define GBMD_STEP_STG(M, NB, MB)                                                                       \
     {                                                                                                  \
@@ -1357,8 +1486,7 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
 #undef GBMD_STEP
     }
     if (props) {
-        k_props_slices<<<S.nrep * PROPS_SPLIT, 256, 0, L.stream>>>(A, S);
-        k_props_finalize<<<S.nrep, 32, 0, L.stream>>>(A, S, 1, 1);
+        k_props_reduce<<<S.nrep * S.props_split, PROPS_THREADS, 0, L.stream>>>(A, S, 1, 1);
     }
     return cudaGetLastError();
 }
@@ -1366,8 +1494,12 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
 cudaError_t launch_forces(const Arrays& A, const Scal& S, const Launch& L, int cur)
 {
     const int g = tile_grid(S, L);
+    // with the list-free step kernel there is no current W: the forces come from the cells too
+    const bool cells = L.step_kernel == 4;
     if (S.mode == MD_FP64) k_forces<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (S.mode == MD_MIXED && cells) k_forces<MD_MIXED, true><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else if (S.mode == MD_MIXED) k_forces<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);
+    else if (cells) k_forces<MD_FP32, true><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else k_forces<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S, cur);
     return cudaGetLastError();
 }
@@ -1382,8 +1514,7 @@ cudaError_t launch_props(const Arrays& A, const Scal& S, const Launch& L, int cu
     if (S.mode == MD_FP64) k_props_tiles<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S);
     else if (S.mode == MD_MIXED) k_props_tiles<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S);
     else k_props_tiles<MD_FP32><<<g, TILE, 0, L.stream>>>(A, S);
-    k_props_slices<<<S.nrep * PROPS_SPLIT, 256, 0, L.stream>>>(A, S);
-    k_props_finalize<<<S.nrep, 32, 0, L.stream>>>(A, S, to_series ? 1 : 0, 0);
+    k_props_reduce<<<S.nrep * S.props_split, PROPS_THREADS, 0, L.stream>>>(A, S, to_series ? 1 : 0, 0);
     return cudaGetLastError();
 }
 

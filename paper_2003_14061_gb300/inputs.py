@@ -7,6 +7,8 @@ numpy's PCG64 generator seeded with the caller's integer.
 Workloads (Sec. 3.1 of the paper describes a cubic grid of atoms with random velocities; the
 workloads here use an fcc lattice instead):
   * ``fcc_lattice``      4 n^3 atoms on an fcc lattice of n^3 unit cells at density rho.
+  * ``cubic_lattice``    N_e^3 atoms on a simple cubic grid at density rho (the paper's initial
+                         state, Sec. 3.1).
   * ``fcc_subset``       N atoms drawn without replacement from the smallest fcc lattice with
                          at least N sites, box scaled so that the density is rho.
   * ``maxwell``          Gaussian velocity components, zero net momentum, rescaled so that
@@ -47,6 +49,16 @@ def fcc_lattice(ncell: int, rho: float):
     L = box_side(n, rho)
     x = _fcc_sites(ncell, L / ncell)
     x = np.mod(x, L)
+    return np.ascontiguousarray(x), np.array([L, L, L])
+
+
+def cubic_lattice(n_edge: int, rho: float):
+    """Simple cubic grid of n_edge^3 atoms at density rho, offset by half a spacing: (x, box)."""
+    n = int(n_edge) ** 3
+    L = box_side(n, rho)
+    g = (np.arange(n_edge, dtype=np.float64) + 0.5) * (L / n_edge)
+    cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
+    x = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
     return np.ascontiguousarray(x), np.array([L, L, L])
 
 

@@ -211,6 +211,29 @@ class MDSystem:
                    int(ckpt_every), ctypes.byref(loss), ctypes.byref(ge), ctypes.byref(gs), gptr)
         return loss.value, ge.value, gs.value, gv
 
+    # -- VACF / MSD of atoms followed by their ids --------------------------------------------
+    def dyn_begin(self, nlag: int, origin_every: int):
+        """Start a VACF / MSD measurement with its device buffer (torch-owned)."""
+        nb = self.lib.md_dyn_workspace_bytes(self.h, int(nlag), int(origin_every))
+        if nb == 0:
+            raise B.MDError(-1, "md_dyn_workspace_bytes", B.last_error())
+        with torch.cuda.device(self.device):
+            self._dyn_ws = torch.empty(int(nb), dtype=torch.uint8, device=self.device)
+        self._dyn_nlag = int(nlag)
+        self._call("md_dyn_begin", ctypes.c_void_p(self._dyn_ws.data_ptr()), int(nb), int(nlag), int(origin_every))
+
+    def dyn_sample(self):
+        self._call("md_dyn_sample")
+
+    def dyn_result(self):
+        """(vacf [nlag], msd [nlag], counts [nlag]): averages per atom and origin."""
+        n = self._dyn_nlag
+        vacf, msd = np.zeros(n), np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        self._call("md_dyn_get", vacf.ctypes.data_as(ctypes.c_void_p), msd.ctypes.data_as(ctypes.c_void_p),
+                   cnt.ctypes.data_as(ctypes.c_void_p))
+        return vacf, msd, cnt
+
     def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0,
                    step_kernel: int = 0):
         """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct;

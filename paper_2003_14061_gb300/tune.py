@@ -4,13 +4,14 @@ The paper found thread-block size to matter little on its GPU and warned that th
 elsewhere (Sec. 4.1 item 2).  On GB300 the residency of the fused step kernel and the number of
 neighbour-matrix loads each thread keeps in flight decide its speed, so they are measured on the
 system itself: every candidate advances the live system by a number of steps timed with CUDA
-events on the library's stream.  All candidates perform the same arithmetic in the same order,
-so tuning never changes the trajectory.
+events on the library's stream.  Step kernels 1-3 and builds 2, 4 and 32 perform the same
+arithmetic in the same order; the list-free step kernel (4) and the sub-cell build (1) sum each
+force in another order, so choosing them changes the trajectory at the rounding level only.
 
 Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch) for the step -- the
 per-thread kernel at register-bound residencies, the shared-memory ring and the staged-neighbour
-kernel at the residencies their shared memory allows -- then build_batch for the neighbour build
-(timed over steps that include rebuilds).  Results are cached per GPU and workload signature in a
+kernel at the residencies their shared memory allows, the list-free kernel -- then build_batch for
+the neighbour build (timed over steps that include rebuilds).  Results are cached per GPU and workload signature in a
 JSON file.
 """
 from __future__ import annotations
@@ -26,8 +27,9 @@ from . import binding as B
 CTAS = (4, 8, 12, 16)          # per-thread step kernel (register-bound residency)
 CTAS_RING = (2, 3, 4, 6)       # shared-memory ring step kernel (shared-memory-bound residency)
 CTAS_STAGED = (4, 6, 8)        # staged-neighbour step kernel (register- and shared-memory-bound)
+CTAS_CELLS = (4, 8, 12)        # list-free step kernel (register-bound residency)
 NBR_BATCH = (2, 4, 8)
-BUILD_BATCH = (2, 4, 32)
+BUILD_BATCH = (1, 2, 4, 32)
 
 
 def signature(system) -> str:
@@ -48,8 +50,10 @@ def _time_steps(system, steps: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
-def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False) -> dict:
-    """Pick ctas_per_sm, nbr_batch and build_batch for this system; returns the choice and timings."""
+def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False,
+         step_kernels=(1, 2, 3, 4)) -> dict:
+    """Pick ctas_per_sm, nbr_batch and build_batch for this system; returns the choice and timings.
+    step_kernels: the step kernels to try (md_adjoint needs one that reads W: 1, 2 or 3)."""
     key = signature(system)
     if cache and os.path.exists(cache):
         try:
@@ -77,10 +81,10 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
     cur = system.tuning()
     best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel")}
     best_ms = trial(**best)
-    kernels = (1,) if system.params.precision == B.MD_FP64 else (1, 2, 3)
+    kernels = (1,) if system.params.precision == B.MD_FP64 else tuple(step_kernels)
     for sk in kernels:
-        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED}[sk]:
-            for nb in NBR_BATCH:
+        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS}[sk]:
+            for nb in (NBR_BATCH if sk != 4 else (2,)):
                 cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk)
                 if json.dumps(cand, sort_keys=True) in trials:
                     continue

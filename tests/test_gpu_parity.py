@@ -77,7 +77,7 @@ def test_cells_bit_exact(name, prec):
     assert np.array_equal(s.cells(), cell)
 
 
-@pytest.mark.parametrize("build", [2, 32])
+@pytest.mark.parametrize("build", [1, 2, 32])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", CASES)
 def test_neighbour_sets_bit_exact(name, prec, build):
@@ -115,12 +115,17 @@ def test_step0_forces_and_energy(name, prec):
     assert np.all(np.abs(np.array(pr["P"]) - op[4:7]) <= ptol)
 
 
+@pytest.mark.parametrize("build", [2, 1])
 @pytest.mark.parametrize("reorder", [100, 0])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name", ["wca2048", "wca1372", "lj1372"])
-def test_trajectory_100_steps(name, prec, reorder):
-    # reorder 0: the atoms are reordered at every rebuild inside the captured graphs
+def test_trajectory_100_steps(name, prec, reorder, build):
+    # reorder 0: the atoms are reordered at every rebuild inside the captured graphs; build 1: the
+    # neighbour matrix from half-side sub-cells (other column order, same sets)
+    if build == 1 and prec == "fp64":
+        pytest.skip("MD_FP64 builds through its own FP64 kernel")
     s, x, v, box, rc, skin = make(name, prec, reorder_every=reorder)
+    s.set_tuning(build_batch=build)
     s.integrate(100)
     xg, vg, _ = s.state()
     p = oracle.pot(rc=rc)
@@ -192,6 +197,23 @@ def test_launch_shapes_do_not_change_results():
         s.integrate(64)
         x, v, _ = s.state()
         assert np.array_equal(x, xr) and np.array_equal(v, vr), (ctas, nb, bb, sk)
+
+
+def test_sub_cell_build_launch_shapes_agree():
+    # the sub-cell build orders each column of W its own way, so its trajectories agree among
+    # themselves bit for bit (every launch shape and step kernel) and with the oracle to the bars
+    def run(ctas, nb, sk):
+        s, x, v, box, rc, skin = make("lj1372", "mixed", reorder_every=0)
+        s.set_tuning(ctas_per_sm=ctas, nbr_batch=nb, build_batch=1, step_kernel=sk)
+        s.integrate(64)
+        xs, vs, _ = s.state()
+        return xs, vs, x, v, box, rc
+    xr, vr, x, v, box, rc = run(8, 2, 1)
+    for ctas, nb, sk in ((4, 4, 1), (12, 8, 1), (4, 4, 2), (8, 2, 3)):
+        xs, vs, *_ = run(ctas, nb, sk)
+        assert np.array_equal(xs, xr) and np.array_equal(vs, vr), (ctas, nb, sk)
+    xo, vo, _, _ = oracle.run(x, v, box, oracle.pot(rc=rc), dt=0.005, nsteps=64, with_props=False)
+    assert np.abs(min_image(xr - xo, box)).max() <= 1e-4 and rel_l2(vr, vo) <= 1e-4
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -385,7 +407,7 @@ def test_batched_replicas(prec):
         off += n
 
 
-@pytest.mark.parametrize("build", [2, 32])
+@pytest.mark.parametrize("build", [1, 2, 32])
 def test_neighbour_overflow_on_rebuild_is_reported(build):
     # atoms pushed into one octant: eight times the density the capacity was sized for
     x, box, rc, skin, T = case("wca1372")
@@ -464,3 +486,53 @@ def test_full_size_sampled(name):
     assert rel_l2(vg, vo) <= 1e-4
     assert abs(p1["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / n) <= 1e-6
     assert p1["rebuilds"] >= 2 and abs(p1["rebuilds"] - (rb + 1)) <= 1
+
+
+# ---------------------------------------------------------------------------------------------
+# the list-free step kernel (step kernel 4: no neighbour matrix, the 27 cells every step)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("name", ["wca2048", "wca1372", "lj1372"])
+def test_list_free_kernel_matches_oracle(name, prec):
+    s, x, v, box, rc, skin = make(name, prec)
+    s.set_tuning(step_kernel=4)                         # reorders by cell at once, then at every rebuild
+    _, _, f = s.state(x=False, v=False, f=True)         # the standalone force pass reads the cells too
+    p = oracle.pot(rc=rc)
+    of, _, _, _ = oracle.forces(x, box, p)
+    assert rel_l2(f, of) <= 1e-5
+    s.integrate(100)
+    xg, vg, _ = s.state()
+    pr = s.props()[0]
+    xo, vo, po, rb = oracle.run(x, v, box, p, dt=0.005, nsteps=100, rule=1, skin=skin)
+    assert np.abs(min_image(xg - xo, box)).max() <= 1e-4
+    assert rel_l2(vg, vo) <= 1e-4
+    assert abs(pr["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / x.shape[0]) <= 1e-6
+    assert pr["reorders"] == pr["rebuilds"] and abs(pr["rebuilds"] - (rb + 2)) <= 2   # +2: creation, switch
+    # back to the neighbour-matrix kernel: W is rebuilt at the switch and the run goes on
+    s.set_tuning(step_kernel=1)
+    s.integrate(16)
+    _, _, f1 = s.state(x=False, v=False, f=True)
+    x1, _, _ = s.state(v=False)
+    of1, _, _, _ = oracle.forces(x1, box, p)
+    assert rel_l2(f1, of1) <= 1e-5
+
+
+def test_list_free_kernel_batched_replicas():
+    specs = inputs.replica_specs(5, 500, 2500, 0.6, 0.9, seed=14)
+    states = [(inputs.perturb(xr, br, 0.08, 80 + r), vr, br)
+              for r, (xr, vr, br) in enumerate(inputs.replica_states(specs, 1.0, seed=14))]
+    n_rep = [sp[0] for sp in specs]
+    x = np.concatenate([st[0] for st in states])
+    v = np.concatenate([st[1] for st in states])
+    s = MDSystem(x, v, n_rep=n_rep, boxes=np.stack([st[2] for st in states]), rc=WCA_RC, skin=0.4,
+                 precision="mixed", props_every=5)
+    s.set_tuning(step_kernel=4)
+    s.integrate(50)
+    xg, vg, _ = s.state()
+    off = 0
+    for xr, vr, br in states:
+        n = xr.shape[0]
+        xo, vo, _, _ = oracle.run(xr, vr, br, oracle.pot(), dt=0.005, nsteps=50, with_props=False)
+        assert np.abs(min_image(xg[off:off + n] - xo, br)).max() <= 1e-4
+        assert rel_l2(vg[off:off + n], vo) <= 1e-4
+        off += n
