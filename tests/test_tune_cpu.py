@@ -34,7 +34,7 @@ class FakeSystem:
 def cost(t):
     # a unique minimum at step kernel 1, 12 CTAs/SM, 4 entries per batch, build batch 4
     c = 1.0 + 0.1 * abs(t["ctas_per_sm"] - 12) + 0.05 * abs(t["nbr_batch"] - 4)
-    c += {1: 0.0, 2: 0.5, 3: 0.7}[t["step_kernel"]] + {2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
+    c += {1: 0.0, 2: 0.5, 3: 0.7, 4: 0.9}[t["step_kernel"]] + {1: 0.1, 2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
     return c
 
 
@@ -51,10 +51,13 @@ def test_search_finds_the_fastest_shape(fake_timing):
     assert res["ms_per_step"] == pytest.approx(1.0)
     assert res["ms_per_step"] == min(res["trials"].values())
     tried = [json.loads(k) for k in res["trials"]]
-    assert {t["step_kernel"] for t in tried} == {1, 2, 3}
+    assert {t["step_kernel"] for t in tried} == {1, 2, 3, 4}
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 1} == set(tune.CTAS)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 2} == set(tune.CTAS_RING)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 3} == set(tune.CTAS_STAGED)
+    assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 4} == set(tune.CTAS_CELLS)
+    assert {t["nbr_batch"] for t in tried if t["step_kernel"] == 4} == {2}
+    assert {t["build_batch"] for t in tried} == set(tune.BUILD_BATCH)
     assert s.tuning()["ctas_per_sm"] == 12 and s.tuning()["build_batch"] == 4
     assert s.steps % 16 == 0                       # whole 16-step graph replays only
 
@@ -62,6 +65,12 @@ def test_search_finds_the_fastest_shape(fake_timing):
 def test_fp64_searches_the_per_thread_kernel_only(fake_timing):
     res = tune.tune(FakeSystem(B.MD_FP64), steps=32)
     assert {json.loads(k)["step_kernel"] for k in res["trials"]} == {1}
+
+
+def test_step_kernels_can_be_restricted(fake_timing):
+    # the adjoint reads the neighbour matrix: its tuning leaves the list-free kernel out
+    res = tune.tune(FakeSystem(), steps=32, step_kernels=(1, 2, 3))
+    assert {json.loads(k)["step_kernel"] for k in res["trials"]} == {1, 2, 3}
 
 
 def test_cache_round_trip(fake_timing, tmp_path):
