@@ -70,9 +70,13 @@ def _load():
         lib.orc_adjoint.argtypes = [i64, dp, dp, dp, P, d, d, i64, dp, dp, dp, dp, dp, dp]
         lib.orc_loss.argtypes = [i64, dp, dp, dp, P, d, d, i64, dp]
         lib.orc_dynamics.argtypes = [i64, dp, dp, dp, P, d, d, i64, i32, i32, i32, dp, dp, dp]
+        C = ctypes.POINTER(Chains)
+        lib.orc_chain_forces.argtypes = [i64, dp, dp, C, dp, dp, dp]
+        lib.orc_run_chains.argtypes = [i64, dp, dp, dp, P, C, d, d, i64, dp]
         for name in ("orc_forces_brute", "orc_forces_cells", "orc_force_on_atoms", "orc_cells",
                      "orc_cell_order", "orc_neighbours", "orc_neighbours_sample", "orc_props", "orc_run", "orc_force_jvp",
-                     "orc_param_grads", "orc_adjoint", "orc_loss", "orc_dynamics"):
+                     "orc_param_grads", "orc_adjoint", "orc_loss", "orc_dynamics", "orc_chain_forces",
+                     "orc_run_chains"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -99,6 +103,16 @@ def pot(eps=1.0, sigma=1.0, rc=2.0 ** (1.0 / 6.0), shift=True, rc_scales_with_si
     if rc_scales_with_sigma is None:
         rc_scales_with_sigma = abs(rc / sigma - 2.0 ** (1.0 / 6.0)) < 1e-12
     return Pot(float(eps), float(sigma), float(rc), int(bool(shift)), int(bool(rc_scales_with_sigma)))
+
+
+class Chains(ctypes.Structure):
+    _fields_ = [("len", ctypes.c_int32), ("pad", ctypes.c_int32), ("kb", ctypes.c_double), ("r0", ctypes.c_double),
+                ("ka", ctypes.c_double), ("kd", ctypes.c_double)]
+
+
+def chains(length, kb=30.0, r0=1.5, ka=0.0, kd=0.0):
+    """Chains of `length` consecutive ids: FENE bonds (kb, r0), bending ka, dihedral kd."""
+    return Chains(int(length), 0, float(kb), float(r0), float(ka), float(kd))
 
 
 def set_threads(n: int) -> None:
@@ -294,3 +308,26 @@ def dynamics(x0, v0, box, p: Pot, mass=1.0, dt=0.005, nsamples=1, every=1, nlag=
                                 _ptr(cnt)), "dynamics")
     with np.errstate(invalid="ignore", divide="ignore"):
         return vacf / (n * cnt), msd / (n * cnt), cnt
+
+
+def chain_forces(x, box, ch: Chains):
+    """(F [n,3], U, W) of the chain terms alone."""
+    x = _f64(x, (-1, 3))
+    box = _f64(box, (3,))
+    f = np.zeros_like(x)
+    U = ctypes.c_double()
+    W = ctypes.c_double()
+    _check(_load().orc_chain_forces(x.shape[0], _ptr(x), _ptr(box), ctypes.byref(ch), _ptr(f), ctypes.byref(U),
+                                    ctypes.byref(W)), "chain_forces")
+    return f, U.value, W.value
+
+
+def run_chains(x, v, box, p: Pot, ch: Chains, mass=1.0, dt=0.005, nsteps=1):
+    """KDK leapfrog with pair and chain forces.  Returns (x, v, props [nsteps+1, 8])."""
+    x = _f64(x, (-1, 3)).copy()
+    v = _f64(v, (-1, 3)).copy()
+    box = _f64(box, (3,))
+    pr = np.zeros((int(nsteps) + 1, NPROPS))
+    _check(_load().orc_run_chains(x.shape[0], _ptr(x), _ptr(v), _ptr(box), ctypes.byref(p), ctypes.byref(ch),
+                                  float(mass), float(dt), int(nsteps), _ptr(pr)), "run_chains")
+    return x, v, pr

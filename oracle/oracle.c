@@ -32,6 +32,9 @@
  *   orc_adjoint         -- reverse-mode derivative of the trajectory loss
  *                          L = (1/S) sum_{n=1..S} U(x_n) + |v_S|^2 through the leapfrog steps,
  *                          with every state stored (no checkpointing).
+ *   orc_chain_forces    -- polymer chains (Sec. 4.3 item 2): FENE bonds, bending and dihedral
+ *                          terms along chains of consecutive ids, forces as -dU/dr per term;
+ *   orc_run_chains      -- orc_run with the chain terms added.
  *   orc_dynamics        -- velocity autocorrelation and mean-square displacement of atoms
  *                          followed by identity (Sec. 4.1 items 1 and 7), from orc_run's
  *                          trajectory, over several time origins.
@@ -957,5 +960,155 @@ int orc_dynamics(int64_t n, const double* x0, const double* v0, const double* bo
         }
     }
     free(x); free(v); free(f); free(dr); free(vo); free(start);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Polymer chains (Sec. 4.3 item 2): atoms linked by elastic bonds, a bond-angle term that     */
+/* depends on adjacent bonds, and an optional dihedral term on three consecutive bonds; the    */
+/* pair potential acts between all atoms, bonded ones included.  The chains are consecutive    */
+/* ids: atom c*len + k (k = 0..len-1) of a system of n atoms, the last chain shorter if len     */
+/* does not divide n.  With b_k = r_{k+1} - r_k (minimum image):                               */
+/*   bond      U = -(1/2) kb R0^2 ln(1 - (|b|/R0)^2)          (FENE)                           */
+/*   angle     U = ka (1 - cos t),  cos t = b_k . b_{k+1} / (|b_k| |b_{k+1}|)  (0: straight)   */
+/*   dihedral  U = kd (1 - cos p),  cos p = m1 . m2 / (|m1| |m2|),  m1 = b_k x b_{k+1},        */
+/*             m2 = b_{k+1} x b_{k+2}                                                          */
+/* The forces are -dU/dr, from the derivatives of |b|, cos t and cos p written out per term;   */
+/* U and the virial W = sum over terms of sum_a r_a . f_a (positions of the term's atoms       */
+/* relative to its first atom) are accumulated.  A dihedral whose bonds are collinear to 1e-12 */
+/* (m1 or m2 of length below 1e-6 |b_{k+1}|^2) contributes nothing.                            */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t len;       /* atoms per chain (0: no chains) */
+    int32_t pad;
+    double kb, r0;     /* FENE stiffness and maximum extension */
+    double ka;         /* bending constant */
+    double kd;         /* dihedral constant */
+} orc_chains;
+
+static void orc_cross(const double* a, const double* b, double* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double orc_dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+int orc_chain_forces(int64_t n, const double* x, const double* box, const orc_chains* ch, double* f,
+                     double* U_out, double* W_out)
+{
+    if (n < 0 || !x || !box || !ch) return ORC_ERR_ARG;
+    double U = 0.0, W = 0.0;
+    if (ch->len >= 2) {
+        for (int64_t s = 0; s < n; s += ch->len) {
+            int64_t e = s + ch->len < n ? s + ch->len : n;       /* chain atoms s .. e-1 */
+            for (int64_t k = s; k + 1 < e; ++k) {               /* bonds (k, k+1) */
+                double b[3];
+                for (int a = 0; a < 3; ++a) b[a] = orc_min_image(x[3 * (k + 1) + a] - x[3 * k + a], box[a]);
+                double r2 = orc_dot3(b, b), q = 1.0 - r2 / (ch->r0 * ch->r0);
+                if (!(q > 0.0)) return ORC_ERR_ARG;                /* a bond beyond R0 */
+                U += -0.5 * ch->kb * ch->r0 * ch->r0 * log(q);
+                double g = ch->kb / q;                              /* f_{k+1} = -g b, f_k = +g b */
+                for (int a = 0; a < 3; ++a) {
+                    if (f) { f[3 * (k + 1) + a] -= g * b[a]; f[3 * k + a] += g * b[a]; }
+                }
+                W += -g * r2;                                       /* b . f_{k+1} */
+            }
+            for (int64_t k = s; k + 2 < e; ++k) {               /* angles (k, k+1, k+2) */
+                double b1[3], b2[3];
+                for (int a = 0; a < 3; ++a) {
+                    b1[a] = orc_min_image(x[3 * (k + 1) + a] - x[3 * k + a], box[a]);
+                    b2[a] = orc_min_image(x[3 * (k + 2) + a] - x[3 * (k + 1) + a], box[a]);
+                }
+                double l1 = sqrt(orc_dot3(b1, b1)), l2 = sqrt(orc_dot3(b2, b2));
+                double c = orc_dot3(b1, b2) / (l1 * l2);
+                U += ch->ka * (1.0 - c);
+                /* dc/db1 = b2/(l1 l2) - c b1/l1^2, dc/db2 = b1/(l1 l2) - c b2/l2^2; F = ka dc/dr */
+                double g1[3], g2[3], fr[3][3];
+                for (int a = 0; a < 3; ++a) {
+                    g1[a] = b2[a] / (l1 * l2) - c * b1[a] / (l1 * l1);
+                    g2[a] = b1[a] / (l1 * l2) - c * b2[a] / (l2 * l2);
+                    fr[0][a] = -ch->ka * g1[a];                     /* r_k enters b1 with a minus */
+                    fr[1][a] = ch->ka * (g1[a] - g2[a]);
+                    fr[2][a] = ch->ka * g2[a];
+                }
+                for (int a = 0; a < 3; ++a) {
+                    if (f) { f[3 * k + a] += fr[0][a]; f[3 * (k + 1) + a] += fr[1][a]; f[3 * (k + 2) + a] += fr[2][a]; }
+                }
+                W += orc_dot3(b1, fr[1]) + (orc_dot3(b1, fr[2]) + orc_dot3(b2, fr[2]));
+            }
+            for (int64_t k = s; k + 3 < e && ch->kd != 0.0; ++k) {   /* dihedrals (k .. k+3) */
+                double b1[3], b2[3], b3[3], m1[3], m2[3];
+                for (int a = 0; a < 3; ++a) {
+                    b1[a] = orc_min_image(x[3 * (k + 1) + a] - x[3 * k + a], box[a]);
+                    b2[a] = orc_min_image(x[3 * (k + 2) + a] - x[3 * (k + 1) + a], box[a]);
+                    b3[a] = orc_min_image(x[3 * (k + 3) + a] - x[3 * (k + 2) + a], box[a]);
+                }
+                orc_cross(b1, b2, m1);
+                orc_cross(b2, b3, m2);
+                double q1 = sqrt(orc_dot3(m1, m1)), q2 = sqrt(orc_dot3(m2, m2)), bb = orc_dot3(b2, b2);
+                if (q1 < 1e-6 * bb || q2 < 1e-6 * bb) continue;
+                double c = orc_dot3(m1, m2) / (q1 * q2);
+                U += ch->kd * (1.0 - c);
+                /* dc/dm1 = m2/(q1 q2) - c m1/q1^2 (and 1 <-> 2); G . (db1 x b2) = db1 . (b2 x G),  */
+                /* G . (b1 x db2) = db2 . (G x b1): dc/db1 = b2 x G1, dc/db2 = G1 x b1 + b3 x G2,    */
+                /* dc/db3 = G2 x b2                                                                  */
+                double G1[3], G2[3], d1[3], d2a[3], d2b[3], d3[3], fr[4][3];
+                for (int a = 0; a < 3; ++a) {
+                    G1[a] = m2[a] / (q1 * q2) - c * m1[a] / (q1 * q1);
+                    G2[a] = m1[a] / (q1 * q2) - c * m2[a] / (q2 * q2);
+                }
+                orc_cross(b2, G1, d1);
+                orc_cross(G1, b1, d2a);
+                orc_cross(b3, G2, d2b);
+                orc_cross(G2, b2, d3);
+                for (int a = 0; a < 3; ++a) {
+                    double d2 = d2a[a] + d2b[a];
+                    fr[0][a] = -ch->kd * d1[a];
+                    fr[1][a] = ch->kd * (d1[a] - d2);
+                    fr[2][a] = ch->kd * (d2 - d3[a]);
+                    fr[3][a] = ch->kd * d3[a];
+                }
+                for (int q = 0; q < 4; ++q)
+                    for (int a = 0; a < 3; ++a)
+                        if (f) f[3 * (k + q) + a] += fr[q][a];
+                double r2[3], r3[3];
+                for (int a = 0; a < 3; ++a) { r2[a] = b1[a] + b2[a]; r3[a] = r2[a] + b3[a]; }
+                W += orc_dot3(b1, fr[1]) + orc_dot3(r2, fr[2]) + orc_dot3(r3, fr[3]);
+            }
+        }
+    }
+    if (U_out) *U_out = U;
+    if (W_out) *W_out = W;
+    return ORC_OK;
+}
+
+/* orc_run with the chain terms added to the pair forces (same KDK steps, props with the chain
+ * energy in U and its virial in W; rule 0 only). */
+int orc_run_chains(int64_t n, double* x, double* v, const double* box, const orc_pot* p, const orc_chains* ch,
+                   double mass, double dt, int64_t nsteps, double* props_out)
+{
+    if (n < 0 || !x || !v || !box || !p || !ch || nsteps < 0 || mass <= 0.0) return ORC_ERR_ARG;
+    size_t n3 = 3 * (size_t)(n > 0 ? n : 1);
+    double* f = (double*)malloc(sizeof(double) * n3);
+    if (!f) return ORC_ERR_MEM;
+    double U, W, Uc, Wc;
+    int rc = orc_forces_cells(n, x, box, p, f, NULL, &U, &W);
+    if (!rc) rc = orc_chain_forces(n, x, box, ch, f, &Uc, &Wc);
+    if (!rc && props_out) orc_fill_props(n, v, box, mass, U + Uc, W + Wc, &props_out[0]);
+    double c = dt / (2.0 * mass);
+    for (int64_t step = 0; step < nsteps && !rc; ++step) {
+        for (int64_t i = 0; i < 3 * n; ++i) {
+            v[i] += c * f[i];
+            x[i] = orc_wrap(x[i] + dt * v[i], box[i % 3]);
+        }
+        rc = orc_forces_cells(n, x, box, p, f, NULL, &U, &W);
+        if (!rc) rc = orc_chain_forces(n, x, box, ch, f, &Uc, &Wc);
+        if (rc) break;
+        for (int64_t i = 0; i < 3 * n; ++i) v[i] += c * f[i];
+        if (props_out) orc_fill_props(n, v, box, mass, U + Uc, W + Wc, &props_out[ORC_NPROPS * (step + 1)]);
+    }
+    free(f);
     return rc;
 }

@@ -15,7 +15,11 @@ Pins used (none re-types the oracle's formula):
   * the sampled checkers used at full size (forces on listed atoms, neighbour sets of listed
     atoms) against the whole-system evaluations pinned above;
   * the pressure with a non-zero virial and the trajectory loss, written out from pinned pieces;
-  * finite differences for the Jacobian, the parameter derivatives and the adjoint.
+  * finite differences for the Jacobian, the parameter derivatives and the adjoint;
+  * the VACF / MSD: free flight in closed form, origin counts, caging at density 1.0;
+  * the polymer chain terms: F = -grad U by finite differences per term, closed forms (FENE bond,
+    straight / right / reversed bends, cis / 90 degree / trans dihedrals), zero net force and
+    torque, the virial as sum r . F, chain boundaries by id, O(dt^2) energy error in a run.
 """
 import json
 import math
@@ -590,3 +594,92 @@ def test_dynamics_caged_vacf_goes_negative():
     assert vacf[t_vmin] < -0.05 * vacf[0] and 0.05 < t_vmin * 0.005 < 0.4
     assert np.all(np.diff(msd[:20]) > 0)             # displacements grow at first ...
     assert msd[1] == pytest.approx(vacf[0] * 0.005 ** 2, rel=0.05)   # ... ballistically
+
+
+# ---------------------------------------------------------------------------------------------
+# polymer chains (Sec. 4.3 item 2): FENE bonds, bending and dihedral terms
+# ---------------------------------------------------------------------------------------------
+def _bent_chain(m=7, seed=3):
+    # a random walk of bond length ~1 with bond angles away from 0 and 180 degrees, mid-box
+    rng = np.random.default_rng(seed)
+    x = [np.array([10.0, 10.0, 10.0])]
+    d = np.array([1.0, 0.0, 0.0])
+    for _ in range(m - 1):
+        while True:
+            e = rng.normal(size=3)
+            e /= np.linalg.norm(e)
+            if 0.2 < np.dot(e, d) < 0.85:
+                break
+        d = e
+        x.append(x[-1] + (0.95 + 0.1 * rng.random()) * d)
+    return np.array(x), np.array([20.0, 20.0, 20.0])
+
+
+@pytest.mark.parametrize("terms", [dict(ka=0.0, kd=0.0), dict(ka=5.0, kd=0.0), dict(ka=0.0, kd=2.0),
+                                   dict(ka=5.0, kd=2.0)])
+def test_chain_forces_are_minus_the_energy_gradient(terms):
+    x, box = _bent_chain()
+    ch = oracle.chains(x.shape[0], **terms)
+    f, U, W = oracle.chain_forces(x, box, ch)
+    h = 1e-6
+    fd = np.zeros_like(x)
+    for i in range(x.shape[0]):
+        for a in range(3):
+            xp = x.copy(); xp[i, a] += h
+            xm = x.copy(); xm[i, a] -= h
+            fd[i, a] = -(oracle.chain_forces(xp, box, ch)[1] - oracle.chain_forces(xm, box, ch)[1]) / (2 * h)
+    assert np.abs(f - fd).max() <= 1e-6 * np.abs(f).max()
+    # an isolated chain: no net force, no net torque, and the virial is sum_a r_a . F_a
+    assert np.abs(f.sum(0)).max() <= 1e-10 * np.abs(f).max()
+    assert np.abs(np.cross(x, f).sum(0)).max() <= 1e-9 * np.abs(f).max() * 20
+    assert W == pytest.approx(float((x * f).sum()), rel=1e-10, abs=1e-10)
+
+
+def test_chain_closed_forms():
+    box = np.array([20.0, 20.0, 20.0])
+    # one FENE bond of length 1 across the boundary: U = -(1/2) 30 1.5^2 ln(1 - 1/2.25),
+    # tension 30 / (1 - 1/2.25) = 54 pulling the atoms together, W = -54
+    x = np.array([[0.4, 5.0, 5.0], [19.4, 5.0, 5.0]])
+    f, U, W = oracle.chain_forces(x, box, oracle.chains(2))
+    assert U == pytest.approx(-0.5 * 30 * 2.25 * math.log(1 - 1 / 2.25), rel=1e-14)
+    assert f[0] == pytest.approx([-54.0, 0, 0], rel=1e-13) and f[1] == pytest.approx([54.0, 0, 0], rel=1e-13)
+    assert W == pytest.approx(-54.0, rel=1e-13)
+    # bending: straight U = 0 and no force; a right angle U = ka; antiparallel bonds U = 2 ka
+    ch = oracle.chains(3, kb=0.0, ka=4.0)
+    for pts, u in (([[5, 5, 5], [6, 5, 5], [7, 5, 5]], 0.0), ([[5, 5, 5], [6, 5, 5], [6, 6, 5]], 4.0)):
+        f, U, _ = oracle.chain_forces(np.array(pts, float), box, ch)
+        assert U == pytest.approx(u, abs=1e-14)
+    f, _, _ = oracle.chain_forces(np.array([[5, 5, 5], [6, 5, 5], [7, 5, 5]], float), box, ch)
+    assert np.abs(f).max() == 0.0
+    # dihedral: cis (p = 0) U = 0, p = 90 degrees U = kd, trans (p = 180) U = 2 kd
+    ch = oracle.chains(4, kb=0.0, kd=3.0)
+    for last, u in (([5, 6, 5], 0.0), ([6, 5, 6], 3.0), ([7, 4, 5], 6.0)):
+        pts = np.array([[5, 6, 5], [5, 5, 5], [6, 5, 5], last], float)
+        _, U, _ = oracle.chain_forces(pts, box, ch)
+        assert U == pytest.approx(u, abs=1e-13)
+
+
+def test_chains_split_by_length_and_run_conserves_energy():
+    # chains are consecutive ids: 3 chains of 5 have 12 bonds, not 14
+    x, box = _bent_chain(m=15, seed=8)
+    ch = oracle.chains(5)
+    _, U, _ = oracle.chain_forces(x, box, ch)
+    U_sep = sum(oracle.chain_forces(x[k:k + 5], box, ch)[1] for k in (0, 5, 10))
+    assert U == pytest.approx(U_sep, rel=1e-14)
+    # chains of 4 (the 4 basis sites of each fcc cell, bonds of 1.26) packed at density 0.7 with
+    # bending and dihedral terms: momentum conserved, energy error bounded and O(dt^2)
+    xs, bx = inputs.fcc_lattice(4, 0.7)
+    xs = inputs.perturb(xs, bx, 0.02, seed=3)
+    n = xs.shape[0]
+    v = inputs.maxwell(n, 1.0, seed=4)
+    ch = oracle.chains(4, ka=2.0, kd=0.5)
+    _, Ub, _ = oracle.chain_forces(xs, bx, ch)
+    assert np.isfinite(Ub)
+    errs = []
+    for dt, ns in ((0.002, 500), (0.001, 1000)):
+        _, _, pr = oracle.run_chains(xs, v, bx, wca(), ch, dt=dt, nsteps=ns)
+        E = pr[:, 0] + pr[:, 1]
+        assert np.abs(pr[:, 4:7]).max() < 1e-9
+        errs.append(np.abs(E - E[0]).max() / abs(E[0]))
+    # (the stiff FENE bonds, k = 30, make the error larger than the fluid's at the same dt)
+    assert errs[0] < 5e-3 and 3.0 < errs[0] / errs[1] < 5.0
