@@ -359,7 +359,7 @@ def run_gb300(args, rank, world, local_rank):
     e2e_steps = min(args.steps, args.e2e_steps)
     se = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
                   rebuild_rule=RULE, props_every=1, **geo)
-    se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch")})
+    se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "build_stage", "step_kernel")})
     se.integrate(32)                                     # capture its graphs outside the timing:
     se.integrate(1)                                      # the 16-step ones and the one-step ones
     se.integrate(1)                                      # from either position buffer
@@ -493,6 +493,8 @@ def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune
     bpa = algorithmic_bytes_per_atom_step(mean_nbrs, precision, rule)
     if fixed and fixed.get("step_kernel") == 4:
         bpa = algorithmic_bytes_per_atom_step(0.0, precision, rule) - 4.0    # no W and no neighbour counts
+    elif fixed and fixed.get("step_kernel") == 5:
+        bpa += 40.0       # half W (mean_nbrs is the half count) + the FP32 force buffers read and cleared
     achieved = bpa * n / (step_ms * 1e-3) / 1e9
     out = {"label": label, "value": n * steps / (ms * 1e-3), "unit": UNIT, "atoms": n, "replicas": s.nrep,
            "steps": steps, "ms_per_step": ms / steps, "precision": precision, "props_every": props_every,
@@ -573,6 +575,10 @@ def measure_forms(args, dev):
     forms["wca4m_mixed_list_free"] = measure_form("WCA fcc 100^3, MIXED, list-free step kernel (27 cells every step)",
                                                   x, v, geo, dev, "mixed", WCA_RC, 0.4, args.form_steps, 200,
                                                   fixed=dict(step_kernel=4, ctas_per_sm=8))
+    # the half neighbour list with Newton's third law (the variant Sec. 2.3 rejects), A/B
+    forms["wca4m_mixed_half_list"] = measure_form("WCA fcc 100^3, MIXED, half neighbour list + atomic reactions",
+                                                  x, v, geo, dev, "mixed", WCA_RC, 0.4, args.form_steps, 200,
+                                                  fixed=dict(step_kernel=5, ctas_per_sm=8))
     # the main workload with the exact-displacement refresh rule (reads the positions at the last
     # rebuild every step)
     forms["wca4m_mixed_disp"] = measure_form("WCA fcc 100^3, MIXED, rebuild on max |x - x_ref| > skin/2", x, v, geo,
@@ -582,6 +588,9 @@ def measure_forms(args, dev):
     x, v, geo = make_inputs("lj16m")
     forms["lj16m_mixed"] = measure_form(w["desc"], x, v, geo, dev, "mixed", w["rc"], w["skin"],
                                         max(args.form_steps // 4, 100), 100)
+    forms["lj16m_mixed_half_list"] = measure_form(w["desc"] + ", half neighbour list + atomic reactions", x, v, geo,
+                                                  dev, "mixed", w["rc"], w["skin"], max(args.form_steps // 8, 50), 100,
+                                                  fixed=dict(step_kernel=5, ctas_per_sm=8, build_batch=32))
     del x, v
     # 512 independent replicas of uneven size in one persistent launch per step
     w = WORKLOADS["batch512"]

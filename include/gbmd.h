@@ -46,8 +46,8 @@ typedef struct md_system md_system;   /* opaque; owned by the library */
  *   MD_FP32  : pair forces, positions and velocities in FP32; reductions in FP64. */
 typedef enum { MD_FP64 = 0, MD_MIXED = 1, MD_FP32 = 2 } md_precision;
 
-/* When the neighbour matrix is rebuilt (Sec. 2.3: "the maximal atom velocity needed to determine
- * when the neighbor matrix needs rebuilding").
+/* When the neighbour matrix is rebuilt (Sec. 2.3 reduces the largest atom speed for this
+ * decision).
  *   MD_REBUILD_VMAX  : D += dt * max_i |v_i| after every position update; rebuild when
  *                      D > skin/2, then D = 0.
  *   MD_REBUILD_DISP  : rebuild when max_i |x_i - x_i(at last rebuild)| > skin/2.
@@ -188,6 +188,31 @@ int md_set_state(md_system* s, const double* x, const double* v);
 int md_get_cells(md_system* s, int32_t* cell);
 int md_get_neighbours(md_system* s, int32_t* counts, int32_t* nbr_ids, int32_t cap);
 
+/* Polymer chains (Sec. 4.3 item 2: atoms linked by elastic bonds, a bond-angle term from adjacent
+ * bonds and an optional dihedral term on three consecutive bonds, all other interactions as
+ * before).  In every replica the atoms of local ids c*length .. c*length + length - 1 form chain
+ * c (the last chain shorter when length does not divide the replica's atoms).  With b the bond
+ * vectors between consecutive atoms of a chain (minimum image):
+ *   bond      U = -(1/2) fene_k fene_r0^2 ln(1 - |b|^2 / fene_r0^2)     (FENE)
+ *   bend      U = bend_k (1 - cos t),  t the angle between consecutive bonds (0 = straight)
+ *   dihedral  U = dihedral_k (1 - cos p),  p the angle between the normals b1 x b2 and b2 x b3
+ *             (skipped while the bonds are collinear to 1e-6)
+ * The pair potential still acts between all atoms, bonded ones included.  Each thread computes
+ * the force on its own atom from every term the atom belongs to (positions of up to three
+ * chain neighbours on each side, found through the permanent ids); U and the virial include the
+ * terms.  FP32 arithmetic as the pair forces; MD_MIXED and MD_FP32 only.  length 0 removes the
+ * chains.  A bond stretched to fene_r0 or beyond gives non-finite forces (MD_ERR_NONFINITE).
+ * md_adjoint refuses systems with chains. */
+typedef struct {
+    int32_t length;        /* atoms per chain (0: no chains) */
+    int32_t pad;
+    double fene_k;         /* FENE stiffness (30 in the usual bead-spring units) */
+    double fene_r0;        /* FENE maximum extension (1.5) */
+    double bend_k;
+    double dihedral_k;
+} md_chains;
+int md_set_chains(md_system* s, const md_chains* c);
+
 /* Waits for the stream and returns the first latched device error (then clears it).  A
  * non-finite value is reported before a neighbour overflow it may have caused. */
 int md_check(md_system* s);
@@ -239,7 +264,18 @@ typedef struct {
                                 against r_c each step, two at a time in packed FP32x2; atoms are
                                 then reordered by cell at every rebuild and W is not built
                                 (md_get_neighbours reports the last W built; md_adjoint refuses
-                                this kernel) */
+                                this kernel);
+                                5 = the half neighbour list with Newton's third law (the variant
+                                Sec. 2.3 rejects): W keeps each pair once, at its lower slot; a
+                                first kernel evaluates each pair once and adds the force to both
+                                atoms (the partner by vector atomic adds into FP32 buffers), the
+                                step kernel then reads and clears the buffers.  The atomics add
+                                in no fixed order, so repeat runs differ in the last bits;
+                                md_get_neighbours reports the half sets; md_adjoint refuses it */
+    int32_t build_stage;     /* neighbour build (build_batch 1, 2, 4): 1 = each thread appends its
+                                column of W in shared memory and the warps write whole rows (128
+                                contiguous bytes per row for 32 atoms; for matrices far larger
+                                than L2), 2 = each entry written to W as found */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);

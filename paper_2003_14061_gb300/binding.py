@@ -28,7 +28,7 @@ EXPORTS = (
     "md_nrep", "md_natoms", "md_nbr_capacity", "md_cells_per_axis", "md_set_tuning", "md_get_tuning",
     "md_destroy", "md_last_error", "md_set_timing", "md_get_timing", "md_forces_static",
     "md_adjoint_workspace_bytes", "md_adjoint", "md_props_latest", "md_debug_set_error",
-    "md_dyn_workspace_bytes", "md_dyn_begin", "md_dyn_sample", "md_dyn_get",
+    "md_dyn_workspace_bytes", "md_dyn_begin", "md_dyn_sample", "md_dyn_get", "md_set_chains",
 )
 NPHASE = 6
 PHASES = ("step", "bin", "reorder", "build", "props", "other")
@@ -66,7 +66,12 @@ class md_props(ctypes.Structure):
 class md_tuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("nbr_batch", ctypes.c_int32),
                 ("build_batch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("step_kernel", ctypes.c_int32)]
+                ("step_kernel", ctypes.c_int32), ("build_stage", ctypes.c_int32)]
+
+
+class md_chains(ctypes.Structure):
+    _fields_ = [("length", ctypes.c_int32), ("pad", ctypes.c_int32), ("fene_k", ctypes.c_double),
+                ("fene_r0", ctypes.c_double), ("bend_k", ctypes.c_double), ("dihedral_k", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -126,6 +131,7 @@ def lib(build_if_missing: bool = True):
             "md_dyn_begin": (ctypes.c_int, [vp, vp, sz, i32, i32]),
             "md_dyn_sample": (ctypes.c_int, [vp]),
             "md_dyn_get": (ctypes.c_int, [vp, vp, vp, vp]),
+            "md_set_chains": (ctypes.c_int, [vp, ctypes.POINTER(md_chains)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)

@@ -169,6 +169,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.f = c.take<double4_32a>(ns);
     a.wvir = c.take<double>(ns);
     a.id = c.take<int32_t>(ns);
+    a.slot_of_id = c.take<int32_t>(size_t(P.n_total));
     a.cell = c.take<int32_t>(ns);
     a.layer = c.take<int32_t>(ns);
     a.nbr_count = c.take<int32_t>(ns);
@@ -177,6 +178,10 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.perm = c.take<int32_t>(ns);
     if (!f64) a.psort = c.take<float4>(ns);
     if (!f64) a.tile_win = c.take<int2>(size_t(P.ntiles) * 9);
+    if (!f64) {
+        a.fbuf = c.take<float4>(ns);
+        a.wbuf = c.take<float>(ns);
+    }
     if (!f64) {
         const size_t nsub = size_t(8) * size_t(P.ncells);
         a.psub = c.take<float4>(ns);
@@ -191,6 +196,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     else a.tmp_p32 = c.take<float4>(ns);
     a.ccount = c.take<int32_t>(size_t(P.ncells));
     a.cstart = c.take<int32_t>(size_t(P.ncells) + 1);
+    if (!f64) a.ckeep = c.take<int2>(size_t(P.ncells));
     a.chunk = c.take<int32_t>(size_t(P.nchunks));
     a.tile_rep = c.take<int32_t>(size_t(P.ntiles));
     a.rb_tiles = c.take<int32_t>(size_t(P.ntiles));
@@ -429,9 +435,11 @@ int apply_tuning(md_system* s)
     s->L.build_block = TILE;
     s->L.nbr_batch = s->tune.nbr_batch;
     s->L.build_batch = s->tune.build_batch;
+    s->L.build_stage = s->tune.build_stage == 1 ? 1 : 0;
     s->L.step_kernel = (s->S.mode == MD_FP64) ? 1 : s->tune.step_kernel;
     // the list-free kernel reads each row of cells as a run of slots: atoms reorder at every rebuild
     s->S.reorder_every = (s->L.step_kernel == 4) ? 0 : s->p.reorder_every;
+    s->S.half_list = (s->L.step_kernel == 5) ? 1 : 0;      // W keeps each pair once
     bulk_shape(s->S, per_sm, s->smem_per_sm, s->smem_per_cta, &s->L.bulk_rows, &s->L.bulk_smem);
     stage_shape(per_sm, s->smem_per_sm, &s->L.stage_cap, &s->L.stage_smem);
     s->L.ctas_req = per_sm;
@@ -677,6 +685,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
     s->tune.step_kernel = 1;
+    s->tune.build_stage = 2;            // 2 = off (0 keeps the current value in md_set_tuning)
     apply_tuning(s);
 
     auto bail = [&](int code) { delete s; return code; };
@@ -766,7 +775,7 @@ int md_integrate(md_system* s, int32_t nsteps)
                 const int rc = capture_graph(s, s->cur, G, mask, &exec);
                 if (rc) return rc;
             }
-            Phase t(s, MD_PHASE_STEP, G + __builtin_popcount(mask));
+            Phase t(s, MD_PHASE_STEP, G * step_kernels(s->S, s->L) + __builtin_popcount(mask));
             const int rc = replay(s, exec);
             if (rc) return rc;
             k += G;
@@ -779,7 +788,7 @@ int md_integrate(md_system* s, int32_t nsteps)
         const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
         if (props) s->host_series_rows += 1;
         {
-            Phase t(s, MD_PHASE_STEP, props ? 2 : 1);
+            Phase t(s, MD_PHASE_STEP, step_kernels(s->S, s->L) + (props ? 1 : 0));
             GBMD_CUDA(launch_step(s->A, s->S, s->L, s->cur, props));
         }
         s->cur ^= 1;
@@ -952,6 +961,25 @@ int md_check(md_system* s)
     return latch_error(s);
 }
 
+int md_set_chains(md_system* s, const md_chains* c)
+{
+    if (!s || !c) return fail(MD_ERR_INVALID_ARG, "system and chains are required");
+    if (c->length < 0) return fail(MD_ERR_INVALID_ARG, "chain length must be >= 0");
+    if (c->length > 0) {
+        if (s->S.mode == MD_FP64) return fail(MD_ERR_INVALID_ARG, "chains need MD_MIXED or MD_FP32");
+        if (!(std::isfinite(c->fene_k) && c->fene_k >= 0.0 && std::isfinite(c->fene_r0) && c->fene_r0 > 0.0 &&
+              std::isfinite(c->bend_k) && std::isfinite(c->dihedral_k)))
+            return fail(MD_ERR_INVALID_ARG, "fene_k >= 0, fene_r0 > 0 and finite bend_k, dihedral_k are required");
+    }
+    s->S.chain_len = c->length;
+    s->S.ch_kb = float(c->fene_k);
+    s->S.ch_r0sq = float(c->fene_r0 * c->fene_r0);
+    s->S.ch_ka = float(c->bend_k);
+    s->S.ch_kd = float(c->dihedral_k);
+    s->drop_graphs();          // the parameters are baked into captured graphs
+    return MD_OK;
+}
+
 int md_debug_set_error(md_system* s, int32_t status)
 {
     if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
@@ -1087,18 +1115,21 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->build_batch && t->build_batch != 1 && t->build_batch != 2 && t->build_batch != 4 && t->build_batch != 32)
         return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2, 4 or 32");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
-    if (t->step_kernel < 0 || t->step_kernel > 4) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0..4");
+    if (t->step_kernel < 0 || t->step_kernel > 5) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0..5");
     const int old_kernel = s->L.step_kernel;
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
     if (t->build_batch) s->tune.build_batch = t->build_batch;
     if (t->use_graph) s->tune.use_graph = t->use_graph;
     if (t->step_kernel) s->tune.step_kernel = t->step_kernel;
+    if (t->build_stage < 0 || t->build_stage > 2) return fail(MD_ERR_INVALID_ARG, "build_stage must be 0, 1 or 2");
+    if (t->build_stage) s->tune.build_stage = t->build_stage;
     s->drop_graphs();          // launch shapes are baked into captured graphs
     int rc = apply_tuning(s);
     if (rc) return rc;
-    if ((s->L.step_kernel == 4) != (old_kernel == 4)) {
-        // into the list-free kernel: atoms reordered by cell now; out of it: W built now
+    if ((s->L.step_kernel == 4) != (old_kernel == 4) || (s->L.step_kernel == 5) != (old_kernel == 5)) {
+        // into the list-free kernel: atoms reordered by cell now; out of it: W built now; into or
+        // out of the half list: W rebuilt with the other half rule
         GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, s->L.step_kernel == 4 ? 1 : 0));
         GBMD_CUDA(launch_rebuild(s->A, s->S, s->L, s->cur, false));
         s->binned_fresh = false;
@@ -1314,8 +1345,9 @@ int md_adjoint(md_system* s, void* d_work, size_t work_bytes, int32_t nsteps, in
     AdjPlan P;
     int rc = adj_plan(s, nsteps, ckpt_every, &P);
     if (rc) return rc;
-    if (s->L.step_kernel == 4)
-        return fail(MD_ERR_INVALID_ARG, "the adjoint walks the neighbour matrix: select step kernel 1, 2 or 3");
+    if (s->L.step_kernel >= 4)
+        return fail(MD_ERR_INVALID_ARG, "the adjoint walks the full neighbour matrix: select step kernel 1, 2 or 3");
+    if (s->S.chain_len) return fail(MD_ERR_INVALID_ARG, "the adjoint covers the pair forces only: no chains");
     const size_t need = carve_adj(s, P, nullptr, nullptr);
     if (!d_work || (reinterpret_cast<uintptr_t>(d_work) & 255u) || work_bytes < need)
         return fail(MD_ERR_WORKSPACE, "adjoint workspace missing, misaligned or below " + std::to_string(need) + " bytes");

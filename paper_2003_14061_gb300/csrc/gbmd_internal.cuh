@@ -95,6 +95,7 @@ struct Arrays {
     double4_32a* f;               // forces and u_i (md_compute_forces)
     double* wvir;             // per-atom virial sum_j r_ij . f_ij (md_compute_forces)
     int32_t* id;
+    int32_t* slot_of_id;      // [n_total] the inverse of id (chain neighbours are found by id)
     int32_t* cell;
     int32_t* layer;
     int32_t* nbr_count;
@@ -102,6 +103,8 @@ struct Arrays {
     float4* xref;             // positions at the last rebuild (rule DISP)
     int32_t* perm;            // cell-ordered slots (the matrix H of Sec. 2.3, flattened)
     float4* psort;            // FP32 positions in cell order, slot in .w (MD_MIXED, MD_FP32)
+    float4* fbuf;             // step kernel 5: FP32 force and u_i accumulated over the half list
+    float* wbuf;              //   and the per-atom virial (zero between steps)
     float4* psub;             // FP32 positions sorted by half-side sub-cell, slot in .w (sub-cell build)
     int32_t* scount;          // per sub-cell (8 per cell): occupancy, then zero again after the scan
     int32_t* sstart;          // per sub-cell + 1: start in psub
@@ -117,6 +120,9 @@ struct Arrays {
     // per cell
     int32_t* ccount;
     int32_t* cstart;
+    int2* ckeep;              // per cell: [start, end) in its replica's cell order at that replica's
+                              // last rebuild (the list-free step kernel reads it every step; cstart
+                              // is recomputed for all cells when any replica rebuilds)
     int32_t* chunk;           // per SCAN_CHUNK cells
     // per tile
     int32_t* tile_rep;
@@ -149,6 +155,9 @@ struct Scal {
     int32_t series_cap;
     int32_t shift;
     int32_t props_split;      // CTAs per replica of the props reduction (1..PROPS_SPLIT_MAX)
+    int32_t half_list;        // 1: W keeps each pair once, at the lower slot (step kernel 5)
+    int32_t chain_len;        // polymer chains (md_set_chains): atoms per chain, 0 = none
+    float ch_kb, ch_r0sq, ch_ka, ch_kd;   // FENE stiffness, R0^2, bend and dihedral constants
     int64_t nsub;             // half-side sub-cells (8 per cell) of the sub-cell build
     int32_t nschunks;
     double dt, mass, c;       // c = dt / (2 m)
@@ -437,6 +446,7 @@ struct Launch {
     int build_block;
     int nbr_batch;            // W entries loaded together per thread in the pair loop (2, 4, 8)
     int ctas_req;             // requested resident CTAs/SM (register bound of the step kernel)
+    int build_stage;          // 1: the thread-per-atom builds stage their columns in shared memory
     int build_batch;          // candidates loaded together per thread in the build (2, 4; 32 = warp per cell;
                               // 1 = thread per atom over half-side sub-cells)
     int step_kernel;          // 1: per-thread loads with L2 prefetch; 2: bulk-copy shared-memory ring;
@@ -482,6 +492,11 @@ cudaError_t launch_dyn_sample(const Arrays& A, const Scal& S, const Launch& L, c
                               int cur);
 
 // step path (kernels_step.cu)
+// launches per step without the props: the half-list pairs and the chain terms run before the step
+inline int step_kernels(const Scal& S, const Launch& L)
+{
+    return (L.step_kernel == 5 ? 2 : 1) + ((S.chain_len && S.mode != MD_FP64) ? 1 : 0);
+}
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props);
 int step_ctas_per_sm(const Scal& S, const Launch& L);     // resident CTAs/SM of the chosen k_step
 // rows of W and dynamic shared memory of the ring kernel for ctas_per_sm resident CTAs/SM

@@ -387,6 +387,10 @@ __global__ void __launch_bounds__(256) k_sort_cells(Arrays A, Scal S, int cur)
             }
             A.perm[q + 1] = key;
         }
+        if (A.ckeep && A.rs[A.cell_rep[c]].rebuild) {
+            const int base = A.cstart[A.rep[A.cell_rep[c]].cell0];
+            A.ckeep[c] = make_int2(b - base, e - base);
+        }
         // the cell-ordered copy of the FP32 positions read by the neighbour build, slot in .w
         if (A.psort && A.rs[A.cell_rep[c]].rebuild) {
             const float4* __restrict__ pos = A.pos32[cur];
@@ -457,6 +461,7 @@ __global__ void __launch_bounds__(TILE) k_reorder_copy(Arrays A, Scal S, int cur
             }
         }
         A.id[slot] = A.tmp_i[0][slot];
+        A.slot_of_id[A.tmp_i[0][slot]] = int32_t(slot);
         A.cell[slot] = A.tmp_i[1][slot];
         const int k = A.cstart[R.cell0] + int(j);
         A.perm[k] = int32_t(slot);
@@ -637,27 +642,43 @@ __global__ void __launch_bounds__(TILE) k_build(Arrays A, Scal S, int cur)
 // load through perm.  x and y of a candidate are adjacent in its float4 and go through packed
 // FP32x2 adds; each lane rounds as the scalar criterion does (a - b is a + (-b)), and the rows,
 // cells and candidates are visited in k_build's order, so W is entry for entry k_build's.
+// With half = 1 (the half list of step kernel 5) only partners of a higher slot are kept: the
+// criterion is exactly antisymmetric in i and j (IEEE subtraction and negation), so every pair
+// is kept once.
 __device__ __forceinline__ void nbr_test(const float4& p, const float2& npxy, float npz, float offx, float offy,
                                          float offz, bool valid, uint32_t code, int me, float rl2, uint32_t*& wp,
-                                         int& m, int cap, int64_t nslots)
+                                         int& m, int cap, int64_t stride, int half)
 {
     const float2 dxy = __fadd2_rn(__fadd2_rn(make_float2(p.x, p.y), npxy), make_float2(offx, offy));
     const float dz = __fadd_rn(__fadd_rn(p.z, npz), offz);
     const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dxy.y, dxy.y, __fmul_rn(dxy.x, dxy.x)));
     const int j = __float_as_int(p.w);
-    if (valid && r2 < rl2 && j != me) {
+    if (valid && r2 < rl2 && (half ? j > me : j != me)) {
         if (m < cap) {
             *wp = (uint32_t(j) << IDX_SHIFT) | code;
-            wp += nslots;
+            wp += stride;
         }
         ++m;
     }
 }
 
-template <int BB>
+// STAGE: a thread appends its column of W to shared memory (stride TILE) instead of W itself,
+// and each warp then writes its columns row by row: 32 consecutive slots of a row are 128
+// contiguous bytes, where entries written as found land one at a time in partly written sectors.
+// Every thread reads back only its own column, so no block barrier is needed.
+__device__ __forceinline__ void flush_columns(const Arrays& A, const Scal& S, const uint32_t* sW, int64_t slot, int mc)
+{
+    const int mw = int(__reduce_max_sync(0xffffffffu, unsigned(mc)));
+    for (int q = 0; q < mw; ++q)
+        if (q < mc) A.W[int64_t(q) * S.nslots + slot] = sW[q * TILE + threadIdx.x];
+}
+
+template <int BB, bool STAGE>
 __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur)
 {
+    extern __shared__ uint32_t sW[];                 // STAGE: [cap][TILE] columns of this tile
     if (!A.g->any_rebuild) return;
+    const int64_t wstride = STAGE ? int64_t(TILE) : S.nslots;
     const float4* __restrict__ pos = A.pos32[cur];
     const float4* __restrict__ ps = A.psort;
     const int32_t* __restrict__ cs = A.cstart;
@@ -689,7 +710,7 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
             const int ncx = R.nc[0];
             const bool inner = cx > 0 && cx < ncx - 1;
             const int me = int(slot);
-            uint32_t* wp = A.W + slot;
+            uint32_t* wp = STAGE ? sW + threadIdx.x : A.W + slot;
             // neighbouring cells whose nearest point is beyond r_c + skin are skipped (as k_build)
             const float dlo2[3] = {pi.x * pi.x, pi.y * pi.y, pi.z * pi.z};
             const float dhi2[3] = {(w0 - pi.x) * (w0 - pi.x), (w1 - pi.y) * (w1 - pi.y), (w2 - pi.z) * (w2 - pi.z)};
@@ -722,7 +743,7 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
                                 const uint32_t c = uint32_t(k >= b1) + uint32_t(k >= b2);   // o_x + 1
                                 const float offx = (k < b1) ? -w0 : ((k < b2) ? 0.0f : w0);
                                 nbr_test(pj[u], npxy, npz, offx, offy, offz, k < ke, codeyz | c, me, rl2, wp, m,
-                                         S.cap, S.nslots);
+                                         S.cap, wstride, S.half_list);
                             }
                         }
                     } else {
@@ -740,7 +761,7 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
 #pragma unroll
                                 for (int u = 0; u < BB; ++u)
                                     nbr_test(pj[u], npxy, npz, offx, offy, offz, k0 + u < e, codeyz | uint32_t(c), me,
-                                             rl2, wp, m, S.cap, S.nslots);
+                                             rl2, wp, m, S.cap, wstride, S.half_list);
                             }
                         }
                     }
@@ -755,6 +776,7 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
             run_sum += m;
             run_max = max(run_max, m);
         }
+        if (STAGE) flush_columns(A, S, sW, slot, active ? min(m, S.cap) : 0);
     }
     if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
 }
@@ -847,10 +869,12 @@ __device__ __forceinline__ float sub_gap2(float l, int j, float h)
     return d * d;
 }
 
-template <int BB>
+template <int BB, bool STAGE>
 __global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
 {
+    extern __shared__ uint32_t sW[];                 // STAGE: [cap][TILE] columns of this tile
     if (!A.g->any_rebuild) return;
+    const int64_t wstride = STAGE ? int64_t(TILE) : S.nslots;
     const float4* __restrict__ pos = A.pos32[cur];
     const float4* __restrict__ ps = A.psub;
     const int32_t* __restrict__ ss = A.sstart;
@@ -887,7 +911,7 @@ __global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
 #pragma unroll
             for (int d = 0; d < 5; ++d) gx[d] = sub_gap2(pi.x, bx + d - 2, h0);
             const int me = int(slot);
-            uint32_t* wp = A.W + slot;
+            uint32_t* wp = STAGE ? sW + threadIdx.x : A.W + slot;
             const float2 npxy = make_float2(-pi.x, -pi.y);
             const float npz = -pi.z;
             for (int dz = 0; dz < 5; ++dz) {
@@ -932,7 +956,7 @@ __global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
                                 const uint32_t c = uint32_t(k >= b1) + uint32_t(k >= b2);   // o_x + 1
                                 const float offx = (k < b1) ? -w0 : ((k < b2) ? 0.0f : w0);
                                 nbr_test(pj[u], npxy, npz, offx, offy, offz, k < ke, codeyz | c, me, rl2, wp, m,
-                                         S.cap, S.nslots);
+                                         S.cap, wstride, S.half_list);
                             }
                         }
                     } else {
@@ -950,7 +974,7 @@ __global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
 #pragma unroll
                                 for (int u = 0; u < BB; ++u)
                                     nbr_test(pj[u], npxy, npz, offx, offy, offz, k0 + u < e, codeyz | uint32_t(ox + 1), me,
-                                             rl2, wp, m, S.cap, S.nslots);
+                                             rl2, wp, m, S.cap, wstride, S.half_list);
                             }
                         }
                     }
@@ -965,6 +989,7 @@ __global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
             run_sum += m;
             run_max = max(run_max, m);
         }
+        if (STAGE) flush_columns(A, S, sW, slot, active ? min(m, S.cap) : 0);
     }
     if (run_r >= 0) flush_stats(&A.rs[run_r].sum_nbrs, &A.rs[run_r].max_nbrs, run_sum, run_max);
 }
@@ -1100,7 +1125,7 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
                         const float dy = __fadd_rn(__fsub_rn(pj.y, pi.y), offy);
                         const float dz = __fadd_rn(__fsub_rn(pj.z, pi.z), offz);
                         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                        if (have && r2 < rl2 && j != i) {
+                        if (have && r2 < rl2 && (S.half_list ? j > i : j != i)) {
                             if (m < S.cap) {
                                 *wp = (uint32_t(j) << IDX_SHIFT) | code;
                                 wp += S.nslots;
@@ -1307,9 +1332,9 @@ void prime_rebuild_grids(const Scal& S, const Launch& L)
     (void)resident_grid<k_bin<MD_MIXED>>(S, L);
     (void)resident_grid<k_bin<MD_FP32>>(S, L);
     (void)resident_grid<k_scatter>(S, L);
-    (void)resident_grid<k_build_sorted<2>>(S, L);
-    (void)resident_grid<k_build_sorted<4>>(S, L);
-    (void)resident_grid<k_build_sub<2>>(S, L);
+    (void)resident_grid<k_build_sorted<2, false>>(S, L);
+    (void)resident_grid<k_build_sorted<4, false>>(S, L);
+    (void)resident_grid<k_build_sub<2, false>>(S, L);
     (void)resident_grid<k_sub_bin>(S, L);
     (void)resident_grid<k_sub_scatter>(S, L);
     (void)resident_grid<k_reorder_gather<MD_FP64>>(S, L);
@@ -1367,6 +1392,26 @@ static bool skip_w(const Scal& S, const Launch& L) { return L.step_kernel == 4 &
 
 int build_kernels(const Scal& S, const Launch& L) { return skip_w(S, L) ? 2 : (L.build_batch == 1 ? 9 : 3); }
 
+// Grid of a staged build kernel: every CTA resident with `smem` bytes of columns each (the
+// occupancy is looked up again when the size changes)
+template <auto Kernel>
+static int staged_grid(const Scal& S, const Launch& L, int smem)
+{
+    static int last_smem = -1, per_sm = 0;
+    if (smem != last_smem) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::min(optin, smem));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, TILE, smem) != cudaSuccess) per_sm = 1;
+        last_smem = smem;
+    }
+    return std::max(1, std::min(L.nsm * std::max(per_sm, 1), S.ntiles));
+}
+
+// staging the columns needs cap x TILE x 4 bytes per CTA: at most 160 KB (cap <= 320)
+static bool stage_w(const Scal& S, const Launch& L) { return L.build_stage && S.cap * TILE * 4 <= 160 * 1024; }
+
 cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, int cur)
 {
     const int g = tile_grid(S, L);
@@ -1378,11 +1423,24 @@ cudaError_t launch_build_only(const Arrays& A, const Scal& S, const Launch& L, i
         k_sub_scatter<<<resident_grid<k_sub_scatter>(S, L), TILE, 0, L.stream>>>(A, S, cur);
         const int gs = int(std::min<int64_t>((S.nsub + 255) / 256, int64_t(L.grid) * 8));
         k_sub_sort<<<std::max(gs, 1), 256, 0, L.stream>>>(A, S);
-        k_build_sub<2><<<resident_grid<k_build_sub<2>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+        if (stage_w(S, L)) {
+            const int sm = S.cap * TILE * 4;
+            k_build_sub<2, true><<<staged_grid<k_build_sub<2, true>>(S, L, sm), TILE, sm, L.stream>>>(A, S, cur);
+        } else {
+            k_build_sub<2, false><<<resident_grid<k_build_sub<2, false>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+        }
     }
     else if (L.build_batch >= 32) k_build_cw<<<std::max(1, L.grid), TILE, 0, L.stream>>>(A, S, cur);
-    else if (L.build_batch >= 4) k_build_sorted<4><<<resident_grid<k_build_sorted<4>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
-    else k_build_sorted<2><<<resident_grid<k_build_sorted<2>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+    else if (stage_w(S, L)) {
+        const int sm = S.cap * TILE * 4;
+        if (L.build_batch >= 4)
+            k_build_sorted<4, true><<<staged_grid<k_build_sorted<4, true>>(S, L, sm), TILE, sm, L.stream>>>(A, S, cur);
+        else
+            k_build_sorted<2, true><<<staged_grid<k_build_sorted<2, true>>(S, L, sm), TILE, sm, L.stream>>>(A, S, cur);
+    }
+    else if (L.build_batch >= 4)
+        k_build_sorted<4, false><<<resident_grid<k_build_sorted<4, false>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
+    else k_build_sorted<2, false><<<resident_grid<k_build_sorted<2, false>>(S, L), TILE, 0, L.stream>>>(A, S, cur);
     k_tile_windows<<<g, TILE, 0, L.stream>>>(A, S, cur, L.step_kernel == 3 ? 1 : 0);   // used by step kernel 3
     k_rebuild_finish<<<1, 256, 0, L.stream>>>(A, S, L.in_graph);
     return cudaGetLastError();

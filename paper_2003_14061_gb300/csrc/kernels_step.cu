@@ -50,6 +50,17 @@ __device__ __forceinline__ float rcp_approx(float x)
 struct AccF { float fx, fy, fz, u, w; };
 struct AccD { double fx, fy, fz, u, w; };
 
+// With polymer chains the chain terms of every atom are first added into the FP32 buffers
+// fbuf / wbuf by k_chain_terms; the force passes add the buffers in and clear them.
+__device__ __forceinline__ void add_buffer(const Arrays& A, int64_t slot, AccF& a)
+{
+    const float4 b = A.fbuf[slot];
+    a.fx += b.x; a.fy += b.y; a.fz += b.z; a.u += b.w;
+    a.w += A.wbuf[slot];
+    A.fbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    A.wbuf[slot] = 0.f;
+}
+
 // One thread per atom over its column of W, NB entries at a time; wr(m) returns the m-th entry
 // and pr(e) the FP32 cell-local position of the neighbour an entry names.
 // The entries of batch b+1 are read together with the position gathers of batch b, so each
@@ -169,8 +180,8 @@ __device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, 
 {
     int cx, cy, cz;
     unpack_cell(__float_as_uint(pi.w), cx, cy, cz);
-    const int32_t* __restrict__ cs = A.cstart;
-    const int64_t sbase = R.slot0 - cs[R.cell0];            // slot of cell-order position k
+    const int2* __restrict__ ck = A.ckeep;                  // [start, end) of each cell in the replica
+    const int64_t sbase = R.slot0;                          // slot of replica cell-order position k
     const int ncx = R.nc[0];
     const float wx = R.wf[0];
     const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
@@ -187,9 +198,9 @@ __device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, 
             // runs [b, e) with their x offsets: one run of three cells, or three at a wrap in x
             const int nrun = inner ? 1 : 3;
             for (int q = 0; q < nrun; ++q) {
-                const int b = inner ? cs[row + cx - 1] : cs[row + xs[q]];
-                const int e = inner ? cs[row + cx + 2] : cs[row + xs[q] + 1];
-                const int b1 = inner ? cs[row + cx] : e, b2 = inner ? cs[row + cx + 1] : e;
+                const int b = inner ? ck[row + cx - 1].x : ck[row + xs[q]].x;
+                const int e = inner ? ck[row + cx + 1].y : ck[row + xs[q]].y;
+                const int b1 = inner ? ck[row + cx].x : e, b2 = inner ? ck[row + cx + 1].x : e;
                 const float oq = inner ? -1.0f : float(q - 1);
                 for (int k0 = b; k0 < e; k0 += 2) {
                     const int k1 = k0 + 1;
@@ -209,6 +220,229 @@ __device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, 
         }
     }
     return AccF{-(fx.x + fx.y), -(fy.x + fy.y), -(fz.x + fz.y), u.x + u.y, w.x + w.y};
+}
+
+// Step kernel 5, first pass: forces over the half neighbour list with Newton's third law (the
+// paper keeps the full list so that F1 reads W coalesced and writes nothing scattered, Sec. 2.3).
+// Every pair is evaluated once, by the atom of the lower slot: its force, energy and virial go to
+// that atom in registers and to the partner by one vector atomic add (force and u) and one scalar
+// atomic add (virial) into fbuf / wbuf; each atom then adds its own sums the same way.  u_i and
+// the virial keep the full-list convention (each pair counted at both atoms).  The atomics add in
+// no fixed order, so results vary between runs in the last bits.
+template <int NB>
+__global__ void __launch_bounds__(TILE) k_half_pairs(Arrays A, Scal S, int cur)
+{
+    const float4* __restrict__ pos = A.pos32[cur];
+    const int64_t ns = S.nslots;
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const Rep& R = A.rep[A.tile_rep[t]];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        if (slot - R.slot0 >= R.n) continue;
+        const float4 pi = __ldg(pos + slot);
+        const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
+        const uint32_t* __restrict__ Wc = A.W + slot;
+        const float wx = R.wf[0], wy4 = 0.25f * R.wf[1], wz16 = 0.0625f * R.wf[2];
+        float fx = 0.f, fy = 0.f, fz = 0.f, u = 0.f, w = 0.f;
+        for (int m0 = 0; m0 < mm; m0 += NB) {
+            uint32_t e[NB];
+            float4 pj[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) e[k] = (m0 + k < mm) ? __ldcs(Wc + int64_t(m0 + k) * ns) : 0u;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] >> IDX_SHIFT)) : pi;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                const float dx = fmaf(offx_raw(e[k]) - 8388609.0f, wx, pj[k].x - pi.x);
+                const float dy = fmaf(offy_raw(e[k]) - 8388612.0f, wy4, pj[k].y - pi.y);
+                const float dz = fmaf(offz_raw(e[k]) - 8388624.0f, wz16, pj[k].z - pi.z);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (m0 + k < mm && r2 < S.rc2f) {
+                    const float ri2 = rcp_approx(r2);
+                    const float sr2 = S.sig2f * ri2;
+                    const float sr6 = sr2 * sr2 * sr2;
+                    const float fs = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;     // g(r^2)
+                    const float ut = fmaf(S.eps4f * sr6, sr6 - 1.0f, -S.ucf);
+                    const float wt = fs * r2;
+                    fx = fmaf(fs, dx, fx);                                  // sum g (x_j - x_i)
+                    fy = fmaf(fs, dy, fy);
+                    fz = fmaf(fs, dz, fz);
+                    u += ut;
+                    w += wt;
+                    const int64_t j = e[k] >> IDX_SHIFT;
+                    atomicAdd(A.fbuf + j, make_float4(fs * dx, fs * dy, fs * dz, ut));   // on j: +g (x_j - x_i)
+                    atomicAdd(A.wbuf + j, wt);
+                }
+            }
+        }
+        atomicAdd(A.fbuf + slot, make_float4(-fx, -fy, -fz, u));
+        atomicAdd(A.wbuf + slot, w);
+    }
+}
+
+// md_compute_forces / md_get_state with step kernel 5: the accumulated half-list forces into the
+// FP64 force array, the buffers cleared for the next step
+__global__ void __launch_bounds__(TILE) k_half_to_f(Arrays A, Scal S)
+{
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const Rep& R = A.rep[A.tile_rep[t]];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        if (slot - R.slot0 >= R.n) continue;
+        const float4 b = A.fbuf[slot];
+        const AccF a{b.x, b.y, b.z, b.w, A.wbuf[slot]};
+        A.f[slot] = make_double4_32a(a.fx, a.fy, a.fz, a.u);
+        A.wvir[slot] = a.w;
+        A.fbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.wbuf[slot] = 0.f;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// polymer chains (md_set_chains; Sec. 4.3 item 2): one thread per atom and all its interactions
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3(const float* a, const float* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Adds to a the force on the atom at `slot` from the chain terms that contain it (the bonds to
+// its chain neighbours, the bends centred on it and on them, the dihedrals through it), its share
+// of their energy (a bond's energy to both atoms, a bend's 2/3 to each of three, a dihedral's 1/2
+// to each of four, so that (1/2) sum_i u_i counts every term once) and of their virial
+// (2 (r_i - r_first) . f_i, r_first the term's first atom).  Positions are relative to the atom:
+// a chain neighbour's cell-local position, found through its permanent id, plus its cell's offset
+// (the nearest periodic image of the cell difference) times the cell side.
+__device__ __forceinline__ void chain_terms(const Arrays& A, const Scal& S, const Rep& R, const float4* pos, int64_t slot,
+                                         float4 pi, AccF& acc)
+{
+    const int q = A.id[slot] - R.id0;
+    const int c0 = (q / S.chain_len) * S.chain_len;
+    const int c1 = min(c0 + S.chain_len, R.n);              // the chain: local ids c0 .. c1-1
+    int ci[3];
+    unpack_cell(__float_as_uint(pi.w), ci[0], ci[1], ci[2]);
+    const float pc[3] = {pi.x, pi.y, pi.z};
+    float r[7][3];                                          // chain atoms q-3 .. q+3
+    bool ok[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+        const int qq = q + d - 3;
+        ok[d] = qq >= c0 && qq < c1;
+        r[d][0] = r[d][1] = r[d][2] = 0.0f;
+        if (d != 3 && ok[d]) {
+            const float4 pj = pos[A.slot_of_id[R.id0 + qq]];
+            int cj[3];
+            unpack_cell(__float_as_uint(pj.w), cj[0], cj[1], cj[2]);
+            const float pp[3] = {pj.x, pj.y, pj.z};
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                int dc = cj[x] - ci[x];
+                if (2 * dc > R.nc[x]) dc -= R.nc[x];
+                if (2 * dc < -R.nc[x]) dc += R.nc[x];
+                r[d][x] = (pp[x] - pc[x]) + float(dc) * R.wf[x];
+            }
+        }
+    }
+    float f[3] = {0.f, 0.f, 0.f}, u = 0.f, w = 0.f;
+    // bonds (i-1, i) and (i, i+1): f_i = -g (r_i - r_{i-1}) and +g (r_{i+1} - r_i)
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        if (!ok[side ? 4 : 2]) continue;
+        const float* o = r[side ? 4 : 2];
+        const float b2 = dot3(o, o), qf = 1.0f - b2 / S.ch_r0sq;
+        const float g = S.ch_kb / qf;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) f[x] += g * o[x];       // towards the partner either way
+        u += -0.5f * S.ch_kb * S.ch_r0sq * logf(qf);
+        if (!side) w += -2.0f * g * b2;                     // r_i - r_first = r_i - r_{i-1}
+    }
+    // bends with first atom s = i-2, i-1, i (the atom is term atom t = i - s)
+    if (S.ch_ka != 0.0f) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int s0 = 3 - t;                             // index of the term's first atom in r
+            if (!(ok[s0] && ok[s0 + 1] && ok[s0 + 2])) continue;
+            float b1[3], b2[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                b1[x] = r[s0 + 1][x] - r[s0][x];
+                b2[x] = r[s0 + 2][x] - r[s0 + 1][x];
+            }
+            const float l1 = sqrtf(dot3(b1, b1)), l2 = sqrtf(dot3(b2, b2));
+            const float c = dot3(b1, b2) / (l1 * l2);
+            float fr[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const float g1 = b2[x] / (l1 * l2) - c * b1[x] / (l1 * l1);
+                const float g2 = b1[x] / (l1 * l2) - c * b2[x] / (l2 * l2);
+                fr[x] = S.ch_ka * (t == 0 ? -g1 : (t == 1 ? g1 - g2 : g2));
+                f[x] += fr[x];
+            }
+            u += (2.0f / 3.0f) * S.ch_ka * (1.0f - c);
+            w += -2.0f * dot3(r[s0], fr);
+        }
+    }
+    // dihedrals with first atom s = i-3 .. i
+    if (S.ch_kd != 0.0f) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int s0 = 3 - t;
+            if (!(ok[s0] && ok[s0 + 1] && ok[s0 + 2] && ok[s0 + 3])) continue;
+            float b1[3], b2[3], b3[3], m1[3], m2[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                b1[x] = r[s0 + 1][x] - r[s0][x];
+                b2[x] = r[s0 + 2][x] - r[s0 + 1][x];
+                b3[x] = r[s0 + 3][x] - r[s0 + 2][x];
+            }
+            cross3(b1, b2, m1);
+            cross3(b2, b3, m2);
+            const float q1 = sqrtf(dot3(m1, m1)), q2 = sqrtf(dot3(m2, m2)), bb = dot3(b2, b2);
+            if (q1 < 1e-6f * bb || q2 < 1e-6f * bb) continue;
+            const float c = dot3(m1, m2) / (q1 * q2);
+            float G1[3], G2[3], d1[3], d2a[3], d2b[3], d3[3], fr[3];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                G1[x] = m2[x] / (q1 * q2) - c * m1[x] / (q1 * q1);
+                G2[x] = m1[x] / (q1 * q2) - c * m2[x] / (q2 * q2);
+            }
+            cross3(b2, G1, d1);
+            cross3(G1, b1, d2a);
+            cross3(b3, G2, d2b);
+            cross3(G2, b2, d3);
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                const float d2 = d2a[x] + d2b[x];
+                fr[x] = S.ch_kd * (t == 0 ? -d1[x] : (t == 1 ? d1[x] - d2 : (t == 2 ? d2 - d3[x] : d3[x])));
+                f[x] += fr[x];
+            }
+            u += 0.5f * S.ch_kd * (1.0f - c);
+            w += -2.0f * dot3(r[s0], fr);
+        }
+    }
+    acc.fx += f[0];
+    acc.fy += f[1];
+    acc.fz += f[2];
+    acc.u += u;
+    acc.w += w;
+}
+
+// The chain terms of every atom into fbuf / wbuf (one thread per atom, its own slot only; run
+// before the force pass that adds the buffers, or after k_half_pairs on the same stream)
+__global__ void __launch_bounds__(TILE) k_chain_terms(Arrays A, Scal S, int cur)
+{
+    const float4* __restrict__ pos = A.pos32[cur];
+    for (int t = blockIdx.x; t < S.ntiles; t += gridDim.x) {
+        const Rep& R = A.rep[A.tile_rep[t]];
+        const int64_t slot = int64_t(t) * TILE + threadIdx.x;
+        if (slot - R.slot0 >= R.n) continue;
+        AccF a{0.f, 0.f, 0.f, 0.f, 0.f};
+        chain_terms(A, S, R, pos, slot, pos[slot], a);
+        const float4 b = A.fbuf[slot];
+        A.fbuf[slot] = make_float4(b.x + a.fx, b.y + a.fy, b.z + a.fz, b.w + a.u);
+        A.wbuf[slot] += a.w;
+    }
 }
 
 // Leapfrog kick and drift of one atom (Sec. 4.3 item 1) from its force a: MD_MIXED advances the
@@ -624,6 +858,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
                 } else {
                     a = force_f32<NB>(A, S, R, pos, slot, pi);
                 }
+                if (S.chain_len) add_buffer(A, slot, a);
                 double v[3], x[3];
                 float v32[3], pn[3];
 #pragma unroll
@@ -701,7 +936,9 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
     __syncwarp();
 }
 
-template <int MODE, bool PROPS, int NB, int MINB, bool CELLS = false>
+// SRC: where the forces come from -- 0 the neighbour matrix W, 1 the 27 cells (step kernel 4),
+// 2 the half-list buffers filled by k_half_pairs (step kernel 5; read and cleared here)
+template <int MODE, bool PROPS, int NB, int MINB, int SRC = 0>
 __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                       int use_cond)
 {
@@ -756,7 +993,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
     // L2 and the claim of the one after it is in flight
     int w0 = claim_now();
     int w1 = (w0 >= 0) ? claim_now() : -1;
-    int c0 = (w0 >= 0 && !CELLS) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
+    int c0 = (w0 >= 0 && SRC == 0) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
     int run_r = -1, run_cnt = 0;
     float run_max = 0.0f;
     while (w0 >= 0) {
@@ -783,7 +1020,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
                 }
                 prefetch_l2(p);
             }
-            if (!CELLS) c1 = __ldcs(A.nbr_count + s1 + lane);
+            if (SRC == 0) c1 = __ldcs(A.nbr_count + s1 + lane);
         }
         const int t = w0 / (TILE / 32);
         const int r = A.tile_rep[t];
@@ -803,8 +1040,18 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         for (int q = 0; q < NPROP; ++q) part[q] = 0.0f;
         if (active) {
             const float4 pi = __ldg(pos + slot);
-            const AccF a = CELLS ? force_f32_cells(A, S, R, pos, slot, pi)
-                                 : force_f32_rows<NB>(A, S, R, pos, slot, pi, min(c0, S.cap));
+            AccF a;
+            if (SRC == 1) {
+                a = force_f32_cells(A, S, R, pos, slot, pi);
+            } else if (SRC == 2) {
+                const float4 fb = __ldcs(A.fbuf + slot);
+                a = AccF{fb.x, fb.y, fb.z, fb.w, __ldcs(A.wbuf + slot)};
+                A.fbuf[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                A.wbuf[slot] = 0.f;
+            } else {
+                a = force_f32_rows<NB>(A, S, R, pos, slot, pi, min(c0, S.cap));
+            }
+            if (S.chain_len && SRC != 2) add_buffer(A, slot, a);
             double v[3], x[3];
             float v32[3], pn[3];
 #pragma unroll
@@ -841,7 +1088,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         if (w1 >= 0) {
             // the rows of W below the next warp-tile's largest count into L2
             const int mw = min(__reduce_max_sync(0xffffffffu, unsigned(c1)), unsigned(S.cap));
-            if (!CELLS)
+            if (SRC == 0)
                 for (int k = lane; k < mw; k += 32) prefetch_l2(A.W + int64_t(k) * S.nslots + int64_t(w1) * 32);
             if (pending) {
                 const int k = __shfl_sync(0xffffffffu, pend, 0);
@@ -979,9 +1226,10 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
             const uint32_t* sw = reinterpret_cast<const uint32_t*>(sb + SL.w) + threadIdx.x;
             const uint32_t* __restrict__ gw = A.W + slot;
             const int64_t ns = S.nslots;
-            const AccF a = pair_loop_f32<NB>(
+            AccF a = pair_loop_f32<NB>(
                 S, R, pi, mm, [=](int m) { return (m < rows) ? sw[m * TILE] : __ldcs(gw + int64_t(m) * ns); },
                 [=](uint32_t e) { return __ldg(pos + (e >> IDX_SHIFT)); });
+            if (S.chain_len) add_buffer(A, slot, a);
             double v[3], x[3];
             float v32[3], pn[3];
 #pragma unroll
@@ -1042,8 +1290,9 @@ __global__ void __launch_bounds__(TILE) k_forces(Arrays A, Scal S, int cur)
             A.wvir[slot] = a.w;
         } else {
             const float4 pi = A.pos32[cur][slot];
-            const AccF a = CELLS ? force_f32_cells(A, S, R, A.pos32[cur], slot, pi)
-                                 : force_f32<4>(A, S, R, A.pos32[cur], slot, pi);
+            AccF a = CELLS ? force_f32_cells(A, S, R, A.pos32[cur], slot, pi)
+                           : force_f32<4>(A, S, R, A.pos32[cur], slot, pi);
+            if (S.chain_len) add_buffer(A, slot, a);
             A.f[slot] = make_double4_32a(a.fx, a.fy, a.fz, a.u);
             A.wvir[slot] = a.w;
         }
@@ -1199,6 +1448,7 @@ __global__ void __launch_bounds__(TILE) k_set_state(Arrays A, Scal S, int cur)
         if (j >= R.n) continue;
         const int64_t id = R.id0 + j;
         A.id[slot] = int32_t(id);
+        A.slot_of_id[id] = int32_t(slot);
         for (int a = 0; a < 3; ++a) {
             A.xl[a][slot] = A.xchg[0][id * 3 + a];     // global position, origin cell (0,0,0)
             double v = A.xchg[1][id * 3 + a];
@@ -1391,25 +1641,30 @@ void stage_shape(int ctas_per_sm, int smem_per_sm, int* cap, int* smem_bytes)
     *smem_bytes = c * 16;
 }
 
-template <int M, int MINB>
-static int occ_cells()
+template <int M, int MINB, int SRC>
+static int occ_src()
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, false, 2, MINB, true>, TILE, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_sm<M, true, 2, MINB, true>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, false, 2, MINB, SRC>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_sm<M, true, 2, MINB, SRC>, TILE, 0);
     return std::max(1, std::min(a, b));
+}
+
+template <int M, int SRC>
+static int occ_src_mb(int mb)
+{
+    return mb == 16 ? occ_src<M, 16, SRC>() : mb == 12 ? occ_src<M, 12, SRC>() : mb == 8 ? occ_src<M, 8, SRC>()
+                                                                                       : occ_src<M, 4, SRC>();
 }
 
 int step_ctas_per_sm(const Scal& S, const Launch& L)
 {
     int occ = 1;
     if (S.mode == MD_FP64) return occ_of<MD_FP64, 2, 4>();
-    if (L.step_kernel == 4) {
+    if (L.step_kernel == 4 || L.step_kernel == 5) {
         const int mb = minb_of(L.ctas_req);
-        if (S.mode == MD_MIXED) return mb == 16 ? occ_cells<MD_MIXED, 16>() : mb == 12 ? occ_cells<MD_MIXED, 12>()
-                                       : mb == 8 ? occ_cells<MD_MIXED, 8>() : occ_cells<MD_MIXED, 4>();
-        return mb == 16 ? occ_cells<MD_FP32, 16>() : mb == 12 ? occ_cells<MD_FP32, 12>()
-               : mb == 8 ? occ_cells<MD_FP32, 8>() : occ_cells<MD_FP32, 4>();
+        if (L.step_kernel == 4) return S.mode == MD_MIXED ? occ_src_mb<MD_MIXED, 1>(mb) : occ_src_mb<MD_FP32, 1>(mb);
+        return S.mode == MD_MIXED ? occ_src_mb<MD_MIXED, 2>(mb) : occ_src_mb<MD_FP32, 2>(mb);
     }
     if (L.step_kernel == 3) {
 #define GBMD_OCC(M, NB, MB) { occ = occ_staged<M, NB, MB>(L.stage_smem); }
@@ -1435,6 +1690,8 @@ int step_ctas_per_sm(const Scal& S, const Launch& L)
 cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur, bool props)
 {
     const int g = std::max(1, std::min(L.grid_step, S.ntiles));
+    if (S.chain_len && S.mode != MD_FP64)
+        k_chain_terms<<<std::max(1, std::min(L.grid, S.ntiles)), TILE, 0, L.stream>>>(A, S, cur);
     if (S.mode != MD_FP64 && L.step_kernel == 2) {
 #define GBMD_STEP_BULK(M, NB)                                                                               \
     {                                                                                                       \
@@ -1444,22 +1701,33 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
         if (S.mode == MD_MIXED) GBMD_DISPATCH_NB(MD_MIXED, GBMD_STEP_BULK)
         else GBMD_DISPATCH_NB(MD_FP32, GBMD_STEP_BULK)
 #undef GBMD_STEP_BULK
-    } else if (S.mode != MD_FP64 && L.step_kernel == 4) {
-#define GBMD_STEP_CELLS(M, MB)                                                                              \
+    } else if (S.mode != MD_FP64 && (L.step_kernel == 4 || L.step_kernel == 5)) {
+        if (L.step_kernel == 5) {
+            // the half-list pairs into the buffers, then the step reads them
+            const int gp = std::max(1, std::min(L.grid, S.ntiles));
+            if (L.nbr_batch >= 4) k_half_pairs<4><<<gp, TILE, 0, L.stream>>>(A, S, cur);
+            else k_half_pairs<2><<<gp, TILE, 0, L.stream>>>(A, S, cur);
+        }
+#define GBMD_STEP_SRC(M, MB, SRC)                                                                           \
     {                                                                                                       \
-        if (props) k_step_sm<M, true, 2, MB, true><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);   \
-        else k_step_sm<M, false, 2, MB, true><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);        \
+        if (props) k_step_sm<M, true, 2, MB, SRC><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);    \
+        else k_step_sm<M, false, 2, MB, SRC><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);         \
     }
-#define GBMD_CELLS_MB(M)                                                                                    \
+#define GBMD_SRC_MB(M, SRC)                                                                                 \
     {                                                                                                       \
         const int mb = minb_of(L.ctas_req);                                                                 \
-        if (mb == 16) GBMD_STEP_CELLS(M, 16) else if (mb == 12) GBMD_STEP_CELLS(M, 12)                      \
-        else if (mb == 8) GBMD_STEP_CELLS(M, 8) else GBMD_STEP_CELLS(M, 4)                                  \
+        if (mb == 16) GBMD_STEP_SRC(M, 16, SRC) else if (mb == 12) GBMD_STEP_SRC(M, 12, SRC)                \
+        else if (mb == 8) GBMD_STEP_SRC(M, 8, SRC) else GBMD_STEP_SRC(M, 4, SRC)                            \
     }
-        if (S.mode == MD_MIXED) GBMD_CELLS_MB(MD_MIXED)
-        else GBMD_CELLS_MB(MD_FP32)
-#undef GBMD_CELLS_MB
-#undef GBMD_STEP_CELLS
+        if (L.step_kernel == 4) {
+            if (S.mode == MD_MIXED) GBMD_SRC_MB(MD_MIXED, 1)
+            else GBMD_SRC_MB(MD_FP32, 1)
+        } else {
+            if (S.mode == MD_MIXED) GBMD_SRC_MB(MD_MIXED, 2)
+            else GBMD_SRC_MB(MD_FP32, 2)
+        }
+#undef GBMD_SRC_MB
+#undef GBMD_STEP_SRC
     } else if (S.mode != MD_FP64 && L.step_kernel == 3) {
 #define GBMD_STEP_STG(M, NB, MB)                                                                       \
     {                                                                                                  \
@@ -1494,8 +1762,16 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
 cudaError_t launch_forces(const Arrays& A, const Scal& S, const Launch& L, int cur)
 {
     const int g = tile_grid(S, L);
-    // with the list-free step kernel there is no current W: the forces come from the cells too
+    // with the list-free step kernel there is no current W: the forces come from the cells too;
+    // with the half list, from its pairs
     const bool cells = L.step_kernel == 4;
+    if (S.mode != MD_FP64 && L.step_kernel == 5) {
+        k_half_pairs<2><<<g, TILE, 0, L.stream>>>(A, S, cur);
+        if (S.chain_len) k_chain_terms<<<g, TILE, 0, L.stream>>>(A, S, cur);
+        k_half_to_f<<<g, TILE, 0, L.stream>>>(A, S);
+        return cudaGetLastError();
+    }
+    if (S.chain_len && S.mode != MD_FP64) k_chain_terms<<<g, TILE, 0, L.stream>>>(A, S, cur);
     if (S.mode == MD_FP64) k_forces<MD_FP64><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else if (S.mode == MD_MIXED && cells) k_forces<MD_MIXED, true><<<g, TILE, 0, L.stream>>>(A, S, cur);
     else if (S.mode == MD_MIXED) k_forces<MD_MIXED><<<g, TILE, 0, L.stream>>>(A, S, cur);

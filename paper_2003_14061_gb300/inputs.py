@@ -52,13 +52,25 @@ def fcc_lattice(ncell: int, rho: float):
     return np.ascontiguousarray(x), np.array([L, L, L])
 
 
-def cubic_lattice(n_edge: int, rho: float):
-    """Simple cubic grid of n_edge^3 atoms at density rho, offset by half a spacing: (x, box)."""
+def cubic_lattice(n_edge: int, rho: float, serpentine: bool = False):
+    """Simple cubic grid of n_edge^3 atoms at density rho, offset by half a spacing: (x, box).
+    serpentine: the sites ordered along a path that reverses direction in every row and plane,
+    so that consecutive sites are lattice neighbours (chains of consecutive ids, bond = spacing)."""
     n = int(n_edge) ** 3
     L = box_side(n, rho)
-    g = (np.arange(n_edge, dtype=np.float64) + 0.5) * (L / n_edge)
-    cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
-    x = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    a = L / n_edge
+    if serpentine:
+        # rows alternate in x within a plane; odd planes walk the plane's path backwards
+        plane = [(x if y % 2 == 0 else n_edge - 1 - x, y) for y in range(n_edge) for x in range(n_edge)]
+        idx = []
+        for z in range(n_edge):
+            for (x, y) in (plane if z % 2 == 0 else plane[::-1]):
+                idx.append((x, y, z))
+        x = (np.array(idx, dtype=np.float64) + 0.5) * a
+    else:
+        g = (np.arange(n_edge, dtype=np.float64) + 0.5) * a
+        cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
+        x = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
     return np.ascontiguousarray(x), np.array([L, L, L])
 
 

@@ -211,6 +211,12 @@ class MDSystem:
                    int(ckpt_every), ctypes.byref(loss), ctypes.byref(ge), ctypes.byref(gs), gptr)
         return loss.value, ge.value, gs.value, gv
 
+    def set_chains(self, length: int, fene_k: float = 30.0, fene_r0: float = 1.5, bend_k: float = 0.0,
+                   dihedral_k: float = 0.0):
+        """Polymer chains of `length` consecutive ids in every replica (0 removes them)."""
+        c = B.md_chains(int(length), 0, float(fene_k), float(fene_r0), float(bend_k), float(dihedral_k))
+        self._call("md_set_chains", ctypes.byref(c))
+
     # -- VACF / MSD of atoms followed by their ids --------------------------------------------
     def dyn_begin(self, nlag: int, origin_every: int):
         """Start a VACF / MSD measurement with its device buffer (torch-owned)."""
@@ -235,11 +241,14 @@ class MDSystem:
         return vacf, msd, cnt
 
     def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0,
-                   step_kernel: int = 0):
+                   step_kernel: int = 0, build_stage: int = 0):
         """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct;
         step_kernel: 1 = per-thread loads with L2 prefetch, 2 = bulk-copy shared-memory ring,
-        3 = staged cell-row windows in shared memory."""
-        t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph), int(step_kernel))
+        3 = staged cell-row windows in shared memory, 4 = list-free (27 cells every step),
+        5 = half neighbour list with atomic reactions; build_stage: 1 = the build writes W rows
+        from shared memory, 2 = entry by entry."""
+        t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph), int(step_kernel),
+                        int(build_stage))
         self._call("md_set_tuning", ctypes.byref(t))
 
     def set_timing(self, enable: bool = True):

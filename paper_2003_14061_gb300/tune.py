@@ -6,12 +6,13 @@ neighbour-matrix loads each thread keeps in flight decide its speed, so they are
 system itself: every candidate advances the live system by a number of steps timed with CUDA
 events on the library's stream.  Step kernels 1-3 and builds 2, 4 and 32 perform the same
 arithmetic in the same order; the list-free step kernel (4) and the sub-cell build (1) sum each
-force in another order, so choosing them changes the trajectory at the rounding level only.
+force in another order, and the half-list kernel (5) adds through atomics in no fixed order, so
+choosing them changes the trajectory at the rounding level only.
 
 Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch) for the step -- the
 per-thread kernel at register-bound residencies, the shared-memory ring and the staged-neighbour
-kernel at the residencies their shared memory allows, the list-free kernel -- then build_batch for
-the neighbour build (timed over steps that include rebuilds).  Results are cached per GPU and workload signature in a
+kernel at the residencies their shared memory allows, the list-free kernel -- then build_batch and
+build_stage for the neighbour build (timed over steps that include rebuilds).  Results are cached per GPU and workload signature in a
 JSON file.
 """
 from __future__ import annotations
@@ -27,9 +28,10 @@ from . import binding as B
 CTAS = (4, 8, 12, 16)          # per-thread step kernel (register-bound residency)
 CTAS_RING = (2, 3, 4, 6)       # shared-memory ring step kernel (shared-memory-bound residency)
 CTAS_STAGED = (4, 6, 8)        # staged-neighbour step kernel (register- and shared-memory-bound)
-CTAS_CELLS = (4, 8, 12)        # list-free step kernel (register-bound residency)
+CTAS_CELLS = (4, 8, 12)        # list-free and half-list step kernels (register-bound residency)
 NBR_BATCH = (2, 4, 8)
 BUILD_BATCH = (1, 2, 4, 32)
+BUILD_STAGE = (2, 1)           # the build writes W entry by entry, or rows from shared memory
 
 
 def signature(system) -> str:
@@ -51,7 +53,7 @@ def _time_steps(system, steps: int) -> float:
 
 
 def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False,
-         step_kernels=(1, 2, 3, 4)) -> dict:
+         step_kernels=(1, 2, 3, 4, 5)) -> dict:
     """Pick ctas_per_sm, nbr_batch and build_batch for this system; returns the choice and timings.
     step_kernels: the step kernels to try (md_adjoint needs one that reads W: 1, 2 or 3)."""
     key = signature(system)
@@ -79,12 +81,12 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
         return ms
 
     cur = system.tuning()
-    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel")}
+    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage")}
     best_ms = trial(**best)
     kernels = (1,) if system.params.precision == B.MD_FP64 else tuple(step_kernels)
     for sk in kernels:
-        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS}[sk]:
-            for nb in (NBR_BATCH if sk != 4 else (2,)):
+        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS, 5: CTAS_CELLS}[sk]:
+            for nb in (NBR_BATCH if sk < 4 else (2,)):
                 cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk)
                 if json.dumps(cand, sort_keys=True) in trials:
                     continue
@@ -92,12 +94,13 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
                 if ms < best_ms:
                     best, best_ms = cand, ms
     for bb in BUILD_BATCH:
-        cand = dict(best, build_batch=bb)
-        if json.dumps(cand, sort_keys=True) in trials:
-            continue
-        ms = trial(**cand)
-        if ms < best_ms:
-            best, best_ms = cand, ms
+        for stage in (BUILD_STAGE if bb != 32 else (best["build_stage"],)):
+            cand = dict(best, build_batch=bb, build_stage=stage)
+            if json.dumps(cand, sort_keys=True) in trials:
+                continue
+            ms = trial(**cand)
+            if ms < best_ms:
+                best, best_ms = cand, ms
     system.set_tuning(**best)
     result = {"best": best, "ms_per_step": best_ms, "trials": trials, "signature": key,
               "seconds": time.perf_counter() - t_start}

@@ -93,7 +93,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"md_params": B.md_params, "md_props": B.md_props, "md_tuning": B.md_tuning}
+    structs = {"md_params": B.md_params, "md_props": B.md_props, "md_tuning": B.md_tuning, "md_chains": B.md_chains}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gbmd.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')

@@ -16,7 +16,8 @@ class FakeParams:
 class FakeSystem:
     def __init__(self, precision=B.MD_MIXED):
         self.params = FakeParams(precision)
-        self.t = {"ctas_per_sm": 8, "nbr_batch": 2, "build_batch": 2, "use_graph": 1, "step_kernel": 1}
+        self.t = {"ctas_per_sm": 8, "nbr_batch": 2, "build_batch": 2, "use_graph": 1, "step_kernel": 1,
+                  "build_stage": 2}
         self.set_calls = []
         self.steps = 0
 
@@ -34,7 +35,8 @@ class FakeSystem:
 def cost(t):
     # a unique minimum at step kernel 1, 12 CTAs/SM, 4 entries per batch, build batch 4
     c = 1.0 + 0.1 * abs(t["ctas_per_sm"] - 12) + 0.05 * abs(t["nbr_batch"] - 4)
-    c += {1: 0.0, 2: 0.5, 3: 0.7, 4: 0.9}[t["step_kernel"]] + {1: 0.1, 2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
+    c += {1: 0.0, 2: 0.5, 3: 0.7, 4: 0.9, 5: 0.6}[t["step_kernel"]] + {1: 0.1, 2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
+    c += {1: 0.0, 2: 0.01}[t["build_stage"]]
     return c
 
 
@@ -47,16 +49,17 @@ def fake_timing(monkeypatch):
 def test_search_finds_the_fastest_shape(fake_timing):
     s = FakeSystem()
     res = tune.tune(s, steps=64)
-    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1}
+    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1, "build_stage": 1}
     assert res["ms_per_step"] == pytest.approx(1.0)
     assert res["ms_per_step"] == min(res["trials"].values())
     tried = [json.loads(k) for k in res["trials"]]
-    assert {t["step_kernel"] for t in tried} == {1, 2, 3, 4}
+    assert {t["step_kernel"] for t in tried} == {1, 2, 3, 4, 5}
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 1} == set(tune.CTAS)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 2} == set(tune.CTAS_RING)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 3} == set(tune.CTAS_STAGED)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 4} == set(tune.CTAS_CELLS)
-    assert {t["nbr_batch"] for t in tried if t["step_kernel"] == 4} == {2}
+    assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 5} == set(tune.CTAS_CELLS)
+    assert {t["nbr_batch"] for t in tried if t["step_kernel"] in (4, 5)} == {2}
     assert {t["build_batch"] for t in tried} == set(tune.BUILD_BATCH)
     assert s.tuning()["ctas_per_sm"] == 12 and s.tuning()["build_batch"] == 4
     assert s.steps % 16 == 0                       # whole 16-step graph replays only
