@@ -359,7 +359,7 @@ def run_gb300(args, rank, world, local_rank):
     e2e_steps = min(args.steps, args.e2e_steps)
     se = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
                   rebuild_rule=RULE, props_every=1, **geo)
-    se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "build_stage", "step_kernel")})
+    se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "build_stage", "step_kernel", "atom_threads")})
     se.integrate(32)                                     # capture its graphs outside the timing:
     se.integrate(1)                                      # the 16-step ones and the one-step ones
     se.integrate(1)                                      # from either position buffer
@@ -616,7 +616,7 @@ def measure_forms(args, dev):
     va = inputs.maxwell(32000, 1.0, seed=6)
     s = MDSystem(xa, va, boxa, device=dev, rc=WCA_RC, skin=0.4, dt=DT, precision="mixed")
     from paper_2003_14061_gb300 import tune as gtune
-    gtune.tune(s, steps=64, step_kernels=(1, 2, 3))        # launch shapes for this 32k-atom system
+    gtune.tune(s, steps=64, step_kernels=(1,))             # launch shapes for this 32k-atom system
     s.adjoint(400, 20)                                     # warm-up (workspace, graphs, lazy loads)
     import torch
     torch.cuda.synchronize()

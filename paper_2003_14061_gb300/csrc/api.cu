@@ -150,6 +150,15 @@ int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const doub
     return MD_OK;
 }
 
+// CTAs per replica of the props reduction: one warp partial per thread of the first pass (32
+// tiles of 4 warps per CTA of 128 threads), so the pass is one memory round
+int32_t props_split(const Plan& P)
+{
+    int32_t max_tiles = 1;
+    for (const Rep& R : P.reps) max_tiles = std::max(max_tiles, R.ntiles);
+    return std::max(1, std::min(PROPS_SPLIT_MAX, (max_tiles + 31) / 32));
+}
+
 size_t carve(const Plan& P, char* base, Arrays* A)
 {
     Carver c{base};
@@ -203,7 +212,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.cell_rep = c.take<int32_t>(size_t(P.ncells));
     a.rb_base = c.take<int32_t>(size_t(P.nrep));
     a.warp_part = c.take<double>(size_t(P.ntiles) * (TILE / 32) * NPROP);
-    a.slice_part = c.take<double>(size_t(P.nrep) * PROPS_SPLIT_MAX * NPROP);
+    a.slice_part = c.take<double>(size_t(P.nrep) * props_split(P) * NPROP);
     a.rep = c.take<Rep>(size_t(P.nrep));
     a.rs = c.take<RepState>(size_t(P.nrep));
     a.props = c.take<md_props>(size_t(P.nrep));
@@ -375,12 +384,7 @@ void fill_scal(md_system* s)
     S.shift = p.shift_energy;
     S.nsub = int64_t(8) * P.ncells;
     S.nschunks = int32_t((S.nsub + SCAN_CHUNK - 1) / SCAN_CHUNK);
-    {
-        // each CTA of the props reduction adds about 128 warp partials per thread pass
-        int32_t max_tiles = 1;
-        for (const Rep& R : P.reps) max_tiles = std::max(max_tiles, R.ntiles);
-        S.props_split = std::max(1, std::min(PROPS_SPLIT_MAX, (max_tiles + 31) / 32));
-    }
+    S.props_split = props_split(P);
     S.dt = p.dt;
     S.mass = p.mass;
     S.c = p.dt / (2.0 * p.mass);
@@ -437,6 +441,7 @@ int apply_tuning(md_system* s)
     s->L.build_batch = s->tune.build_batch;
     s->L.build_stage = s->tune.build_stage == 1 ? 1 : 0;
     s->L.step_kernel = (s->S.mode == MD_FP64) ? 1 : s->tune.step_kernel;
+    s->L.atom_threads = (s->S.mode == MD_FP64 || s->L.step_kernel != 1) ? 1 : s->tune.atom_threads;
     // the list-free kernel reads each row of cells as a run of slots: atoms reorder at every rebuild
     s->S.reorder_every = (s->L.step_kernel == 4) ? 0 : s->p.reorder_every;
     s->S.half_list = (s->L.step_kernel == 5) ? 1 : 0;      // W keeps each pair once
@@ -686,6 +691,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     s->tune.use_graph = 1;
     s->tune.step_kernel = 1;
     s->tune.build_stage = 2;            // 2 = off (0 keeps the current value in md_set_tuning)
+    s->tune.atom_threads = 1;
     apply_tuning(s);
 
     auto bail = [&](int code) { delete s; return code; };
@@ -775,7 +781,8 @@ int md_integrate(md_system* s, int32_t nsteps)
                 const int rc = capture_graph(s, s->cur, G, mask, &exec);
                 if (rc) return rc;
             }
-            Phase t(s, MD_PHASE_STEP, G * step_kernels(s->S, s->L) + __builtin_popcount(mask));
+            Phase t(s, MD_PHASE_STEP,
+                    G * step_kernels(s->S, s->L) + (s->S.mode == MD_FP64 ? __builtin_popcount(mask) : 0));
             const int rc = replay(s, exec);
             if (rc) return rc;
             k += G;
@@ -788,7 +795,7 @@ int md_integrate(md_system* s, int32_t nsteps)
         const bool props = s->p.props_every > 0 && (s->host_step % s->p.props_every == 0);
         if (props) s->host_series_rows += 1;
         {
-            Phase t(s, MD_PHASE_STEP, step_kernels(s->S, s->L) + (props ? 1 : 0));
+            Phase t(s, MD_PHASE_STEP, step_kernels(s->S, s->L) + (props && s->S.mode == MD_FP64 ? 1 : 0));
             GBMD_CUDA(launch_step(s->A, s->S, s->L, s->cur, props));
         }
         s->cur ^= 1;
@@ -1116,14 +1123,17 @@ int md_set_tuning(md_system* s, const md_tuning* t)
         return fail(MD_ERR_INVALID_ARG, "build_batch must be 1, 2, 4 or 32");
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (t->step_kernel < 0 || t->step_kernel > 5) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0..5");
+    if (t->build_stage < 0 || t->build_stage > 2) return fail(MD_ERR_INVALID_ARG, "build_stage must be 0, 1 or 2");
+    if (t->atom_threads && t->atom_threads != 1 && t->atom_threads != 2 && t->atom_threads != 4)
+        return fail(MD_ERR_INVALID_ARG, "atom_threads must be 1, 2 or 4");
     const int old_kernel = s->L.step_kernel;
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
     if (t->build_batch) s->tune.build_batch = t->build_batch;
     if (t->use_graph) s->tune.use_graph = t->use_graph;
     if (t->step_kernel) s->tune.step_kernel = t->step_kernel;
-    if (t->build_stage < 0 || t->build_stage > 2) return fail(MD_ERR_INVALID_ARG, "build_stage must be 0, 1 or 2");
     if (t->build_stage) s->tune.build_stage = t->build_stage;
+    if (t->atom_threads) s->tune.atom_threads = t->atom_threads;
     s->drop_graphs();          // launch shapes are baked into captured graphs
     int rc = apply_tuning(s);
     if (rc) return rc;

@@ -33,7 +33,7 @@ constexpr int IDX_SHIFT = 6;              // W entry: slot << 6 | (o_z+1) << 4 |
 constexpr int64_t MAX_SLOTS = int64_t(1) << 26;
 constexpr int MAX_NC = 1023;
 constexpr int SCAN_CHUNK = 2048;          // cells per block of the prefix sum
-constexpr int PROPS_SPLIT_MAX = 256;      // CTAs per replica in the first level of the final sums
+constexpr int PROPS_SPLIT_MAX = 2048;     // CTAs per replica in the first level of the final sums
 constexpr int ADJ_VPART = 128;            // blocks of the |v_S|^2 partial sums
 
 enum ErrBits { ERR_NBR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
@@ -72,7 +72,9 @@ struct RepState {             // per replica, mutable on the device
     int64_t sum_nbrs;         // sum m_i at the last rebuild
     int64_t reorders;         // reorders since creation or md_set_state
     int32_t props_done;       // CTAs of the props reduction that have stored their slice
-    int32_t pad;
+    unsigned int pvmax2;      // props step (MD_MIXED / MD_FP32): max |v_n|^2, as float bits
+    long long pacc[NPROP - 1];// props step: the sums in fixed point (2^-24), added by every warp
+    double pbig[NPROP - 1];   // props step: warp sums too large for the fixed point (FP64 atomics)
 };
 
 struct Global {               // device-wide words
@@ -451,6 +453,7 @@ struct Launch {
                               // 1 = thread per atom over half-side sub-cells)
     int step_kernel;          // 1: per-thread loads with L2 prefetch; 2: bulk-copy shared-memory ring;
                               // 3: as 1, with each tile's neighbour positions staged in shared memory
+    int atom_threads;         // step kernel 1: lanes per atom in the pair loop (1, 2, 4)
     int bulk_rows;            // rows of W staged per tile by the ring (step_kernel 2)
     int bulk_smem;            // dynamic shared memory of the ring kernel, bytes
     int stage_cap;            // neighbour positions staged per tile (step_kernel 3)

@@ -8,8 +8,10 @@
 //              cell-local position.  Per tile, the maximum speed (or displacement) is reduced;
 //              the CTA that completes a replica's last tile (the "last block" pattern of
 //              Sec. 2.3, an atomic counter after a memory fence) updates the refresh criterion
-//              and raises the rebuild flag.  With PROPS, the tile also writes FP64 partial sums
-//              of U, K, virial and momentum (F2).
+//              and raises the rebuild flag.  With PROPS, the step also forms F2 (U, K, virial,
+//              momentum): MD_FP64 tiles write FP64 partial sums for k_props_reduce; the MD_MIXED
+//              and MD_FP32 kernels add their warp sums in fixed point and the warp that completes
+//              a replica writes its props (no further launch).
 //   k_step_sm  the same for MD_MIXED and MD_FP32 (step kernel 1): warps take 32-slot warp-tiles
 //              from the slot range of the SM they run on, so the warps of an SM gather from one
 //              neighbourhood held in its L1.  k_step runs MD_FP64 and step kernel 3.
@@ -19,8 +21,8 @@
 //              ring filled by cp.async.bulk (step kernel 2).  The four forms share the pair loop
 //              and the kick-drift, so they give bit-identical trajectories.
 //   k_forces   F1 alone: f_i, u_i and the per-atom virial at the current positions.
-//   k_props_*  F2 and the other measured quantities: per-tile FP64 partials, then one CTA per
-//              replica sums them in a fixed order (deterministic).
+//   k_props_*  F2 outside the step (and for MD_FP64 steps): per-warp FP64 partials, then CTA
+//              slices per replica summed in a fixed order (deterministic).
 #include <algorithm>
 #include <type_traits>
 
@@ -140,6 +142,53 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
                                           const float4* __restrict__ pos, int64_t slot, float4 pi)
 {
     return force_f32_rows<NB>(A, S, R, pos, slot, pi, min(__ldcs(A.nbr_count + slot), S.cap));
+}
+
+// The pair loop of one warp-tile (slots base .. base + 31, all of one replica) with T lanes per
+// atom (T = 2 or 4): in pass p the lanes g T .. g T + T - 1 take atom p 32/T + g, lane t of them
+// the entries t, t + T, t + 2T, ... of its column, and the T partial sums are added by xor
+// shuffles (the same bits in all T lanes).  Consecutive entries of a column name atoms close
+// together in slot order, so the 32 gathers of one instruction (32/T atoms, T consecutive entries
+// each) touch fewer 128-byte lines than 32 atoms' m-th entries do.  The force of the atom in slot
+// base + L ends in lane L, which then integrates it as the one-lane-per-atom kernel does.
+// cnt: the neighbour count of slot base + lane (0 for slots past the replica's atoms).
+template <int NB, int T>
+__device__ __forceinline__ AccF force_f32_tpa(const Arrays& A, const Scal& S, const Rep& R,
+                                              const float4* __restrict__ pos, int64_t base, int cnt)
+{
+    constexpr int G = 32 / T;                                 // atoms per pass
+    const int lane = threadIdx.x & 31;
+    const int t = lane % T, g = lane / T;
+    const int64_t ns = S.nslots;
+    AccF out{0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int p = 0; p < T; ++p) {
+        const int ia = p * G + g;                             // the atom of this lane's group
+        const int c = __shfl_sync(0xffffffffu, cnt, ia);
+        const int64_t slot = base + ia;
+        const int mm = min(c, S.cap);
+        const int mine = (mm > t) ? (mm - t + T - 1) / T : 0;
+        const float4 pi = (mm > 0) ? __ldg(pos + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t* __restrict__ Wc = A.W + int64_t(t) * ns + slot;
+        const int64_t step = int64_t(T) * ns;
+        AccF a = pair_loop_f32<NB>(S, R, pi, mine, [=](int k) { return __ldcs(Wc + int64_t(k) * step); },
+                                   [=](uint32_t e) { return __ldg(pos + (e >> IDX_SHIFT)); });
+#pragma unroll
+        for (int o = 1; o < T; o <<= 1) {
+            a.fx += __shfl_xor_sync(0xffffffffu, a.fx, o);
+            a.fy += __shfl_xor_sync(0xffffffffu, a.fy, o);
+            a.fz += __shfl_xor_sync(0xffffffffu, a.fz, o);
+            a.u += __shfl_xor_sync(0xffffffffu, a.u, o);
+            a.w += __shfl_xor_sync(0xffffffffu, a.w, o);
+        }
+        // lane L holds atom L after pass L / G, from the first lane of group L % G
+        const int src = (lane % G) * T;
+        const float fx = __shfl_sync(0xffffffffu, a.fx, src), fy = __shfl_sync(0xffffffffu, a.fy, src);
+        const float fz = __shfl_sync(0xffffffffu, a.fz, src), u = __shfl_sync(0xffffffffu, a.u, src);
+        const float w = __shfl_sync(0xffffffffu, a.w, src);
+        if (lane / G == p) out = AccF{fx, fy, fz, u, w};
+    }
+    return out;
 }
 
 // Two pairs (lanes x and y) of the FP32 pair loop: g(r^2) with the in-range masks, accumulated
@@ -607,12 +656,112 @@ __device__ __forceinline__ void warp_partials_store(T (&p)[NPROP], double* dst)
 // own stores.
 __device__ __forceinline__ double* warp_slot(const Arrays& A, int64_t warp_tile) { return A.warp_part + warp_tile * NPROP; }
 
+// The props of replica r from its sums (acc[0] = sum u_i, acc[1] = sum |v|^2, acc[2] = sum w_i,
+// acc[3..5] = sum v, acc[NPROP-1] = max |v|^2), with the constant factors U = sum u_i / 2,
+// K = m sum v^2 / 2, W = sum w_i / 2, P = m sum v; with to_series also the time-series row.  One
+// thread.
+__device__ void write_props(const Arrays& A, const Scal& S, int r, const double (&acc)[NPROP], int step_lag,
+                            int to_series)
+{
+    const Rep& R = A.rep[r];
+    RepState& st = A.rs[r];
+    const double U = 0.5 * acc[0], K = 0.5 * S.mass * acc[1], W = 0.5 * acc[2];
+    const double V = R.L[0] * R.L[1] * R.L[2];
+    md_props pr;
+    pr.U = U;
+    pr.K = K;
+    pr.E_per_atom = (U + K) / double(R.n);
+    pr.virial = W;
+    pr.pressure = (2.0 * K + W) / (3.0 * V);
+    pr.P[0] = S.mass * acc[3]; pr.P[1] = S.mass * acc[4]; pr.P[2] = S.mass * acc[5];
+    pr.vmax = sqrt(acc[NPROP - 1]);
+    pr.mean_nbrs = double(st.sum_nbrs) / double(R.n);
+    pr.step = st.step - step_lag;
+    pr.rebuilds = st.rebuilds;
+    pr.max_cell_occ = st.max_occ;
+    pr.max_nbrs = st.max_nbrs;
+    pr.reorders = st.reorders;
+    A.props[r] = pr;
+    if (to_series) {
+        // ring of series_cap rows laid out [row][replica][column]: the latest row of every
+        // replica is contiguous (one copy reads it)
+        const int row = st.series_rows % S.series_cap;
+        double* o = A.series + (int64_t(row) * S.nrep + r) * SERIES_COLS;
+        o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
+        o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
+        st.series_rows += 1;
+    }
+}
+
+// Props fused into the MD_MIXED / MD_FP32 step kernels, in fixed point: each warp-tile's FP32
+// warp sums (lane 4q holds quantity q) are rounded to multiples of 2^-24 and added to one int64
+// per lane; each warp adds its totals to the replica's int64 sums with atomics, and the warp that
+// completes the replica writes the props.  Integer sums do not depend on the order, so the props
+// are the same bits whichever warp computed which warp-tile, in every step kernel.  The step
+// 2^-24 is below the rounding of the FP32 warp sums themselves (for a sum of order 1, half an ulp
+// is 6e-8); the range, 2^39 = 5.5e11 per replica, is hundreds of times what a 1e9-atom state at
+// T = 1 sums to.  A warp sum of 2^31 or more (overlapping atoms) is added in FP64 instead, so it
+// cannot wrap the integers.  The largest |v|^2 goes through an atomic maximum.
+constexpr float PROPS_FIX = 16777216.0f;            // 2^24
+constexpr float PROPS_FIX_MAX = 2147483648.0f;      // 2^31: larger warp sums go to pbig
+struct PropsAcc {
+    long long a;                                    // this lane's quantity (lane 4q: quantity q)
+    float vm;                                       // max |v|^2 seen by the warp
+};
+
+__device__ __forceinline__ void props_warp_add(const Arrays& A, int r, float (&p)[NPROP], PropsAcc& pa)
+{
+    int q;
+    float vm;
+    const float a1 = warp_partials(p, q, vm);
+    if ((threadIdx.x & 3) == 0 && q != NPROP - 1) {
+        if (fabsf(a1) < PROPS_FIX_MAX) pa.a += __float2ll_rn(a1 * PROPS_FIX);
+        else atomicAdd(&A.rs[r].pbig[q], double(a1));   // also NaN, which then shows in the props
+    }
+    pa.vm = fmaxf(pa.vm, vm);
+}
+
+// the warp's sums into replica r (all lanes; each lane fences its atomics)
+__device__ __forceinline__ void props_warp_flush(const Arrays& A, int r, PropsAcc& pa)
+{
+    const int lane = threadIdx.x & 31;
+    if ((lane & 3) == 0 && (lane >> 2) < NPROP - 1 && pa.a != 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&A.rs[r].pacc[lane >> 2]), static_cast<unsigned long long>(pa.a));
+    if (lane == 0) atomicMax(&A.rs[r].pvmax2, __float_as_uint(pa.vm));
+    __threadfence();
+    pa.a = 0;
+    pa.vm = 0.0f;
+}
+
+// one warp-tile's props: FP64 lanes (MD_FP64) store the warp's partials for k_props_reduce, FP32
+// lanes add them to the warp's fixed-point sums
+__device__ __forceinline__ void props_take(const Arrays&, int, double (&p)[NPROP], PropsAcc&, double* dst)
+{
+    warp_partials_store(p, dst);
+}
+__device__ __forceinline__ void props_take(const Arrays& A, int r, float (&p)[NPROP], PropsAcc& pa, double*)
+{
+    props_warp_add(A, r, p, pa);
+}
+
 // Refresh criterion and step bookkeeping, run by one thread of the CTA that completed the last
-// tile of replica r in this launch.
+// tile of replica r in this launch.  With props (fixed-point path), first the props of the step.
 __device__ void finish_replica_step(const Arrays& A, const Scal& S, int r, cudaGraphConditionalHandle cond,
-                                    int use_cond)
+                                    int use_cond, int props = 0)
 {
     RepState& st = A.rs[r];
+    if (props) {
+        double acc[NPROP];
+#pragma unroll
+        for (int q = 0; q < NPROP - 1; ++q) {
+            acc[q] = double(static_cast<long long>(atomicExch(reinterpret_cast<unsigned long long*>(&st.pacc[q]), 0ull))) *
+                         (1.0 / 16777216.0) +
+                     __ldcg(&st.pbig[q]);
+            st.pbig[q] = 0.0;
+        }
+        acc[NPROP - 1] = double(__uint_as_float(atomicExch(&st.pvmax2, 0u)));
+        write_props(A, S, r, acc, 0, 1);
+    }
     st.tiles_done = 0;
     const float m2 = __uint_as_float(atomicExch(&st.vmax2, 0u));
     if (!(m2 <= 3.0e38f)) atomicOr(&A.g->err, ERR_NONFINITE);
@@ -646,8 +795,10 @@ __device__ void finish_replica_step(const Arrays& A, const Scal& S, int r, cudaG
 // and the number of tiles it completed.  The CTA that brings the count to the replica's tile
 // total runs the refresh bookkeeping (the last-block pattern).  All threads of the CTA call this.
 __device__ __forceinline__ void flush_replica(const Arrays& A, const Scal& S, int r, float run_max, int tiles,
-                                              float* sh, cudaGraphConditionalHandle cond, int use_cond)
+                                              float* sh, cudaGraphConditionalHandle cond, int use_cond,
+                                              PropsAcc* pa = nullptr)
 {
+    if (pa) props_warp_flush(A, r, *pa);
     const float m = tile_max(run_max, sh);
     if (threadIdx.x == 0) {
         atomicMax(&A.rs[r].vmax2, __float_as_uint(m));
@@ -655,7 +806,7 @@ __device__ __forceinline__ void flush_replica(const Arrays& A, const Scal& S, in
         const int done = atomicAdd(&A.rs[r].tiles_done, tiles) + tiles;
         if (done == A.rep[r].ntiles) {
             __threadfence();
-            finish_replica_step(A, S, r, cond, use_cond);
+            finish_replica_step(A, S, r, cond, use_cond, pa ? 1 : 0);
         }
     }
     __syncthreads();
@@ -703,6 +854,8 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
     // into the replica's counters once per replica (one fence per CTA, not per tile)
     int run_r = -1, run_tiles = 0;
     float run_max = 0.0f;
+    PropsAcc pa{0, 0.0f};
+    PropsAcc* const pfix = (PROPS && MODE != MD_FP64) ? &pa : nullptr;
     for (int t = t_begin; t < t_end; ++t) {
         if (MODE != MD_FP64) {
             if (t + 1 < t_end) {
@@ -735,7 +888,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
         {
             const int r_t = A.tile_rep[t];
             if (r_t != run_r) {
-                if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+                if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond, pfix);
                 run_r = r_t;
                 run_tiles = 0;
                 run_max = 0.0f;
@@ -891,9 +1044,9 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
         }
         run_max = fmaxf(run_max, metric);
         run_tiles += 1;
-        if (PROPS) warp_partials_store(part, warp_slot(A, int64_t(t) * (TILE / 32) + (threadIdx.x >> 5)));
+        if (PROPS) props_take(A, run_r, part, pa, warp_slot(A, int64_t(t) * (TILE / 32) + (threadIdx.x >> 5)));
     }
-    if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+    if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond, pfix);
     if (STG && stg_timeout) atomicOr(&A.g->err, ERR_TIMEOUT);
 }
 
@@ -908,8 +1061,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step(Arrays A, Scal S, int cur, 
 // range is exhausted takes warp-tiles from any range with some left, so every warp-tile is
 // computed exactly once whatever the placement of the CTAs.  The last warp to finish resets the
 // counters for the next step.  Per atom the arithmetic is k_step's, bit for bit, and so are the
-// props: each warp stores its partial sums and the last of a tile's four warps adds them up in
-// warp order, as k_step's tile reduction does.
+// props: the fixed-point sums do not depend on which warp took which warp-tile.
 __device__ __forceinline__ int ld_relaxed_gpu(const int* p)
 {
     int v;
@@ -921,8 +1073,13 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int* p)
 // the refresh metric and the number of warp-tiles; the warp that completes the replica's
 // warp-tiles runs the refresh bookkeeping.
 __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& S, int r, float run_max, int wtiles,
-                                                   cudaGraphConditionalHandle cond, int use_cond)
+                                                   cudaGraphConditionalHandle cond, int use_cond,
+                                                   PropsAcc* pa = nullptr)
 {
+    if (pa) {
+        props_warp_flush(A, r, *pa);
+        __syncwarp();
+    }
     const float m = warp_max(run_max);
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&A.rs[r].vmax2, __float_as_uint(m));
@@ -930,7 +1087,7 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
         const int done = atomicAdd(&A.rs[r].tiles_done, wtiles) + wtiles;
         if (done == A.rep[r].ntiles * (TILE / 32)) {
             __threadfence();
-            finish_replica_step(A, S, r, cond, use_cond);
+            finish_replica_step(A, S, r, cond, use_cond, pa ? 1 : 0);
         }
     }
     __syncwarp();
@@ -938,10 +1095,12 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
 
 // SRC: where the forces come from -- 0 the neighbour matrix W, 1 the 27 cells (step kernel 4),
 // 2 the half-list buffers filled by k_half_pairs (step kernel 5; read and cleared here)
-template <int MODE, bool PROPS, int NB, int MINB, int SRC = 0>
+// TPA: lanes per atom in the pair loop (force_f32_tpa; SRC 0 only)
+template <int MODE, bool PROPS, int NB, int MINB, int SRC = 0, int TPA = 1>
 __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                       int use_cond)
 {
+    static_assert(TPA == 1 || SRC == 0, "lanes per atom > 1 read the neighbour matrix");
     static_assert(MODE != MD_FP64, "MD_FP64 steps run k_step");
     const int nxt = cur ^ 1;
     const int lane = threadIdx.x & 31;
@@ -996,6 +1155,8 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
     int c0 = (w0 >= 0 && SRC == 0) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
     int run_r = -1, run_cnt = 0;
     float run_max = 0.0f;
+    PropsAcc pa{0, 0.0f};
+    PropsAcc* const pfix = PROPS ? &pa : nullptr;
     while (w0 >= 0) {
         int pend = 0;
         const bool pending = home_open && w1 >= 0;
@@ -1025,7 +1186,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         const int t = w0 / (TILE / 32);
         const int r = A.tile_rep[t];
         if (r != run_r) {
-            if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond);
+            if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond, pfix);
             run_r = r;
             run_cnt = 0;
             run_max = 0.0f;
@@ -1038,10 +1199,14 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         float part[NPROP];
 #pragma unroll
         for (int q = 0; q < NPROP; ++q) part[q] = 0.0f;
+        AccF a_tpa;
+        if (TPA > 1) a_tpa = force_f32_tpa<NB, TPA>(A, S, R, pos, int64_t(w0) * 32, active ? c0 : 0);
         if (active) {
             const float4 pi = __ldg(pos + slot);
             AccF a;
-            if (SRC == 1) {
+            if (TPA > 1) {
+                a = a_tpa;
+            } else if (SRC == 1) {
                 a = force_f32_cells(A, S, R, pos, slot, pi);
             } else if (SRC == 2) {
                 const float4 fb = __ldcs(A.fbuf + slot);
@@ -1083,7 +1248,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         }
         run_max = fmaxf(run_max, metric);
         run_cnt += 1;
-        if (PROPS) warp_partials_store(part, warp_slot(A, w0));   // w0 = t * TILE / 32 + warp of the tile
+        if (PROPS) props_warp_add(A, r, part, pa);
         int w2 = -1;
         if (w1 >= 0) {
             // the rows of W below the next warp-tile's largest count into L2
@@ -1101,7 +1266,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         w1 = w2;
         c0 = c1;                                 // read one warp-tile ahead
     }
-    if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond);
+    if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond, pfix);
     // the last warp of the launch resets the counters; the next launch is ordered after this one
     if (lane == 0) {
         __threadfence();
@@ -1194,13 +1359,15 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
     bool timed_out = false;
     int run_r = -1, run_tiles = 0;
     float run_max = 0.0f;
+    PropsAcc pa{0, 0.0f};
+    PropsAcc* const pfix = PROPS ? &pa : nullptr;
     for (int t = t_begin; t < t_end; ++t) {
         const int st = (t - t_begin) & 1;
         const int c2 = (t + 2 < t_end) ? __ldcs(A.nbr_count + int64_t(t + 2) * TILE + threadIdx.x) : 0;
         {
             const int r_t = A.tile_rep[t];
             if (r_t != run_r) {
-                if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+                if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond, pfix);
                 run_r = r_t;
                 run_tiles = 0;
                 run_max = 0.0f;
@@ -1261,14 +1428,14 @@ __global__ void __launch_bounds__(TILE, 2) k_step_bulk(Arrays A, Scal S, int cur
         }
         run_max = fmaxf(run_max, metric);
         run_tiles += 1;
-        if (PROPS) warp_partials_store(part, warp_slot(A, int64_t(t) * (TILE / 32) + warp));
+        if (PROPS) props_warp_add(A, run_r, part, pa);
         // release the stage (every thread is past its reads of it), then refill it with tile t+2
         const int wm = warp_max_i(c2);
         if (lane == 0) sh_mm[st][warp] = wm;
         __syncthreads();
         if (threadIdx.x == 0 && t + 2 < t_end && !timed_out) issue(t + 2, st, block_mmax(st));
     }
-    if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond);
+    if (run_r >= 0) flush_replica(A, S, run_r, run_max, run_tiles, sh_max, cond, use_cond, pfix);
     if (timed_out) atomicOr(&A.g->err, ERR_TIMEOUT);
 }
 
@@ -1397,34 +1564,8 @@ __global__ void __launch_bounds__(PROPS_THREADS) k_props_reduce(Arrays A, Scal S
     if (threadIdx.x != 0) return;
 #pragma unroll
     for (int q = 0; q < NPROP; ++q) acc[q] = sh[0][q];
-    RepState& st = A.rs[r];
-    st.props_done = 0;                               // ready for the next reduction
-    const double U = 0.5 * acc[0], K = 0.5 * S.mass * acc[1], W = 0.5 * acc[2];
-    const double V = R.L[0] * R.L[1] * R.L[2];
-    md_props pr;
-    pr.U = U;
-    pr.K = K;
-    pr.E_per_atom = (U + K) / double(R.n);
-    pr.virial = W;
-    pr.pressure = (2.0 * K + W) / (3.0 * V);
-    pr.P[0] = S.mass * acc[3]; pr.P[1] = S.mass * acc[4]; pr.P[2] = S.mass * acc[5];
-    pr.vmax = sqrt(acc[NPROP - 1]);
-    pr.mean_nbrs = double(st.sum_nbrs) / double(R.n);
-    pr.step = st.step - step_lag;
-    pr.rebuilds = st.rebuilds;
-    pr.max_cell_occ = st.max_occ;
-    pr.max_nbrs = st.max_nbrs;
-    pr.reorders = st.reorders;
-    A.props[r] = pr;
-    if (to_series) {
-        // ring of series_cap rows laid out [row][replica][column]: the latest row of every
-        // replica is contiguous (one copy reads it)
-        const int row = st.series_rows % S.series_cap;
-        double* o = A.series + (int64_t(row) * S.nrep + r) * SERIES_COLS;
-        o[0] = double(pr.step); o[1] = U; o[2] = K; o[3] = W; o[4] = pr.pressure;
-        o[5] = pr.P[0]; o[6] = pr.P[1]; o[7] = pr.P[2]; o[8] = pr.vmax;
-        st.series_rows += 1;
-    }
+    A.rs[r].props_done = 0;                          // ready for the next reduction
+    write_props(A, S, r, acc, step_lag, to_series);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1443,7 +1584,8 @@ __global__ void __launch_bounds__(TILE) k_set_state(Arrays A, Scal S, int cur)
             st.D = 0.0; st.vmax2 = 0u; st.rebuild = 0; st.reorder = 0; st.vhalf = 0;
             st.tiles_done = 0; st.max_nbrs = 0; st.max_occ = 0; st.series_rows = 0;
             st.step = 0; st.rebuilds = 0; st.last_reorder = 0; st.sum_nbrs = 0; st.reorders = 0;
-            st.props_done = 0;
+            st.props_done = 0; st.pvmax2 = 0u;
+            for (int q = 0; q < NPROP - 1; ++q) { st.pacc[q] = 0; st.pbig[q] = 0.0; }
         }
         if (j >= R.n) continue;
         const int64_t id = R.id0 + j;
@@ -1650,6 +1792,35 @@ static int occ_src()
     return std::max(1, std::min(a, b));
 }
 
+template <int M, int NB, int MINB, int TPA>
+static int occ_tpa()
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, false, NB, MINB, 0, TPA>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_sm<M, true, NB, MINB, 0, TPA>, TILE, 0);
+    return std::max(1, std::min(a, b));
+}
+
+// step kernel 1 with 2 or 4 lanes per atom: entries per batch 2 or 4 (8 maps to 4)
+#define GBMD_DISPATCH_TPA(M, FN)                                                          \
+    {                                                                                     \
+        const int mb = minb_of(L.ctas_req);                                               \
+        const bool nb4 = L.nbr_batch >= 4;                                                \
+        if (L.atom_threads >= 4) {                                                        \
+            if (nb4) {                                                                    \
+                if (mb == 16) FN(M, 4, 16, 4) else if (mb == 12) FN(M, 4, 12, 4) else if (mb == 8) FN(M, 4, 8, 4) else FN(M, 4, 4, 4) \
+            } else {                                                                      \
+                if (mb == 16) FN(M, 2, 16, 4) else if (mb == 12) FN(M, 2, 12, 4) else if (mb == 8) FN(M, 2, 8, 4) else FN(M, 2, 4, 4) \
+            }                                                                             \
+        } else {                                                                          \
+            if (nb4) {                                                                    \
+                if (mb == 16) FN(M, 4, 16, 2) else if (mb == 12) FN(M, 4, 12, 2) else if (mb == 8) FN(M, 4, 8, 2) else FN(M, 4, 4, 2) \
+            } else {                                                                      \
+                if (mb == 16) FN(M, 2, 16, 2) else if (mb == 12) FN(M, 2, 12, 2) else if (mb == 8) FN(M, 2, 8, 2) else FN(M, 2, 4, 2) \
+            }                                                                             \
+        }                                                                                 \
+    }
+
 template <int M, int SRC>
 static int occ_src_mb(int mb)
 {
@@ -1665,6 +1836,13 @@ int step_ctas_per_sm(const Scal& S, const Launch& L)
         const int mb = minb_of(L.ctas_req);
         if (L.step_kernel == 4) return S.mode == MD_MIXED ? occ_src_mb<MD_MIXED, 1>(mb) : occ_src_mb<MD_FP32, 1>(mb);
         return S.mode == MD_MIXED ? occ_src_mb<MD_MIXED, 2>(mb) : occ_src_mb<MD_FP32, 2>(mb);
+    }
+    if (L.step_kernel == 1 && L.atom_threads > 1) {
+#define GBMD_OCC(M, NB, MB, T) { occ = occ_tpa<M, NB, MB, T>(); }
+        if (S.mode == MD_MIXED) GBMD_DISPATCH_TPA(MD_MIXED, GBMD_OCC)
+        else GBMD_DISPATCH_TPA(MD_FP32, GBMD_OCC)
+#undef GBMD_OCC
+        return occ;
     }
     if (L.step_kernel == 3) {
 #define GBMD_OCC(M, NB, MB) { occ = occ_staged<M, NB, MB>(L.stage_smem); }
@@ -1749,11 +1927,22 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
             if (props) k_step<MD_FP64, true, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);
             else k_step<MD_FP64, false, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);
         }
+        else if (L.atom_threads > 1) {
+#define GBMD_STEP_TPA(M, NB, MB, T)                                                                           \
+    {                                                                                                          \
+        if (props) k_step_sm<M, true, NB, MB, 0, T><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);   \
+        else k_step_sm<M, false, NB, MB, 0, T><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);         \
+    }
+            if (S.mode == MD_MIXED) GBMD_DISPATCH_TPA(MD_MIXED, GBMD_STEP_TPA)
+            else GBMD_DISPATCH_TPA(MD_FP32, GBMD_STEP_TPA)
+#undef GBMD_STEP_TPA
+        }
         else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
         else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)
 #undef GBMD_STEP
     }
-    if (props) {
+    if (props && S.mode == MD_FP64) {
+        // MD_MIXED / MD_FP32 step kernels write the props themselves (fixed-point sums)
         k_props_reduce<<<S.nrep * S.props_split, PROPS_THREADS, 0, L.stream>>>(A, S, 1, 1);
     }
     return cudaGetLastError();

@@ -9,11 +9,12 @@ arithmetic in the same order; the list-free step kernel (4) and the sub-cell bui
 force in another order, and the half-list kernel (5) adds through atomics in no fixed order, so
 choosing them changes the trajectory at the rounding level only.
 
-Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch) for the step -- the
-per-thread kernel at register-bound residencies, the shared-memory ring and the staged-neighbour
-kernel at the residencies their shared memory allows, the list-free kernel -- then build_batch and
-build_stage for the neighbour build (timed over steps that include rebuilds).  Results are cached per GPU and workload signature in a
-JSON file.
+Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch, atom_threads) for the step
+-- the per-thread kernel at register-bound residencies with 1, 2 or 4 lanes per atom, the list-free
+and half-list kernels, and on request the shared-memory ring and the staged-neighbour kernel (2
+and 3, slower on every measured workload) at the residencies their shared memory allows -- then
+build_batch and build_stage for the neighbour build (timed over steps that include rebuilds).
+Results are cached per GPU and workload signature in a JSON file.
 """
 from __future__ import annotations
 
@@ -30,6 +31,8 @@ CTAS_RING = (2, 3, 4, 6)       # shared-memory ring step kernel (shared-memory-b
 CTAS_STAGED = (4, 6, 8)        # staged-neighbour step kernel (register- and shared-memory-bound)
 CTAS_CELLS = (4, 8, 12)        # list-free and half-list step kernels (register-bound residency)
 NBR_BATCH = (2, 4, 8)
+NBR_BATCH_TPA = (2, 4)         # with 2 or 4 lanes per atom
+ATOM_THREADS = (2, 4)
 BUILD_BATCH = (1, 2, 4, 32)
 BUILD_STAGE = (2, 1)           # the build writes W entry by entry, or rows from shared memory
 
@@ -53,9 +56,10 @@ def _time_steps(system, steps: int) -> float:
 
 
 def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False,
-         step_kernels=(1, 2, 3, 4, 5)) -> dict:
-    """Pick ctas_per_sm, nbr_batch and build_batch for this system; returns the choice and timings.
-    step_kernels: the step kernels to try (md_adjoint needs one that reads W: 1, 2 or 3)."""
+         step_kernels=(1, 4, 5)) -> dict:
+    """Pick the step kernel and its launch shape, then the build's, for this system; returns the
+    choice and timings.  step_kernels: the step kernels to try (md_adjoint needs one that reads W:
+    1, 2 or 3)."""
     key = signature(system)
     if cache and os.path.exists(cache):
         try:
@@ -81,13 +85,21 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
         return ms
 
     cur = system.tuning()
-    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage")}
+    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage",
+                                "atom_threads")}
     best_ms = trial(**best)
-    kernels = (1,) if system.params.precision == B.MD_FP64 else tuple(step_kernels)
+    fp64 = system.params.precision == B.MD_FP64
+    kernels = (1,) if fp64 else tuple(step_kernels)
+    shapes = []                                    # (step kernel, lanes per atom, residencies, batches)
     for sk in kernels:
-        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS, 5: CTAS_CELLS}[sk]:
-            for nb in (NBR_BATCH if sk < 4 else (2,)):
-                cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk)
+        ctas = {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS, 5: CTAS_CELLS}[sk]
+        shapes.append((sk, 1, ctas, NBR_BATCH if sk < 4 else (2,)))
+        if sk == 1 and not fp64:
+            shapes += [(1, t, CTAS, NBR_BATCH_TPA) for t in ATOM_THREADS]
+    for sk, tpa, ctas_set, nbs in shapes:
+        for ctas in ctas_set:
+            for nb in nbs:
+                cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk, atom_threads=tpa)
                 if json.dumps(cand, sort_keys=True) in trials:
                     continue
                 ms = trial(**cand)
