@@ -276,14 +276,6 @@ typedef struct {
                                 column of W in shared memory and the warps write whole rows (128
                                 contiguous bytes per row for 32 atoms; for matrices far larger
                                 than L2), 2 = each entry written to W as found */
-    int32_t atom_threads;    /* step kernel 1 (MD_MIXED, MD_FP32): lanes per atom in the pair loop,
-                                1, 2 or 4.  With T > 1 the T lanes of an atom take the entries
-                                t, t + T, ... of its column of W and add their sums by warp
-                                shuffles; each lane then integrates its own atom as with 1.  The
-                                gathers of one instruction then read T consecutive entries of
-                                32/T atoms, which name atoms close together in memory, so they
-                                touch fewer cache lines (for long columns, e.g. LJ at r_c = 2.5).
-                                The summation order, and so the last bits of a force, depend on T */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);

@@ -441,7 +441,6 @@ int apply_tuning(md_system* s)
     s->L.build_batch = s->tune.build_batch;
     s->L.build_stage = s->tune.build_stage == 1 ? 1 : 0;
     s->L.step_kernel = (s->S.mode == MD_FP64) ? 1 : s->tune.step_kernel;
-    s->L.atom_threads = (s->S.mode == MD_FP64 || s->L.step_kernel != 1) ? 1 : s->tune.atom_threads;
     // the list-free kernel reads each row of cells as a run of slots: atoms reorder at every rebuild
     s->S.reorder_every = (s->L.step_kernel == 4) ? 0 : s->p.reorder_every;
     s->S.half_list = (s->L.step_kernel == 5) ? 1 : 0;      // W keeps each pair once
@@ -691,7 +690,6 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     s->tune.use_graph = 1;
     s->tune.step_kernel = 1;
     s->tune.build_stage = 2;            // 2 = off (0 keeps the current value in md_set_tuning)
-    s->tune.atom_threads = 1;
     apply_tuning(s);
 
     auto bail = [&](int code) { delete s; return code; };
@@ -1124,8 +1122,6 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (t->step_kernel < 0 || t->step_kernel > 5) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0..5");
     if (t->build_stage < 0 || t->build_stage > 2) return fail(MD_ERR_INVALID_ARG, "build_stage must be 0, 1 or 2");
-    if (t->atom_threads && t->atom_threads != 1 && t->atom_threads != 2 && t->atom_threads != 4)
-        return fail(MD_ERR_INVALID_ARG, "atom_threads must be 1, 2 or 4");
     const int old_kernel = s->L.step_kernel;
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
@@ -1133,7 +1129,6 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->use_graph) s->tune.use_graph = t->use_graph;
     if (t->step_kernel) s->tune.step_kernel = t->step_kernel;
     if (t->build_stage) s->tune.build_stage = t->build_stage;
-    if (t->atom_threads) s->tune.atom_threads = t->atom_threads;
     s->drop_graphs();          // launch shapes are baked into captured graphs
     int rc = apply_tuning(s);
     if (rc) return rc;

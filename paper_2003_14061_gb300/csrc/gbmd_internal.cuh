@@ -453,7 +453,6 @@ struct Launch {
                               // 1 = thread per atom over half-side sub-cells)
     int step_kernel;          // 1: per-thread loads with L2 prefetch; 2: bulk-copy shared-memory ring;
                               // 3: as 1, with each tile's neighbour positions staged in shared memory
-    int atom_threads;         // step kernel 1: lanes per atom in the pair loop (1, 2, 4)
     int bulk_rows;            // rows of W staged per tile by the ring (step_kernel 2)
     int bulk_smem;            // dynamic shared memory of the ring kernel, bytes
     int stage_cap;            // neighbour positions staged per tile (step_kernel 3)

@@ -46,6 +46,23 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// 1/r^2 for the pair terms: the approximation above refined by one Newton-Raphson step for the
+// reciprocal, y <- y + y (1 - x y), which leaves about half an ulp of error with no bias.  Without
+// it u(r) inherits the approximation's error several times over (r^-12 = (r^-2)^6), and summed
+// over millions of pairs of a dense fluid that came to 2.4e-6 per atom in the energy.  Lanes
+// whose r^2 is 0 (padding, masked afterwards) give NaN here, never used.
+__device__ __forceinline__ float2 rcp2_nr(float2 x)
+{
+    const float2 y = make_float2(rcp_approx(x.x), rcp_approx(x.y));
+    const float2 e = __ffma2_rn(make_float2(-x.x, -x.y), y, make_float2(1.0f, 1.0f));
+    return __ffma2_rn(y, e, y);
+}
+__device__ __forceinline__ float rcp_nr(float x)
+{
+    const float y = rcp_approx(x);
+    return __fmaf_rn(y, __fmaf_rn(-x, y, 1.0f), y);
+}
+
 // ------------------------------------------------------------------------------------------
 // pair loops
 // ------------------------------------------------------------------------------------------
@@ -103,7 +120,7 @@ __device__ __forceinline__ AccF pair_loop_f32(const Scal& S, const Rep& R, float
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const bool in0 = (m0 + k < mm) && r2.x < S.rc2f;
             const bool in1 = (m0 + k + 1 < mm) && r2.y < S.rc2f;
-            const float2 ri2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+            const float2 ri2 = rcp2_nr(r2);
             const float2 sr2 = __fmul2_rn(sig2, ri2);
             const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
             float2 fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(eps48, sr6), __fadd2_rn(sr6, make_float2(-0.5f, -0.5f))), ri2);
@@ -144,53 +161,6 @@ __device__ __forceinline__ AccF force_f32(const Arrays& A, const Scal& S, const 
     return force_f32_rows<NB>(A, S, R, pos, slot, pi, min(__ldcs(A.nbr_count + slot), S.cap));
 }
 
-// The pair loop of one warp-tile (slots base .. base + 31, all of one replica) with T lanes per
-// atom (T = 2 or 4): in pass p the lanes g T .. g T + T - 1 take atom p 32/T + g, lane t of them
-// the entries t, t + T, t + 2T, ... of its column, and the T partial sums are added by xor
-// shuffles (the same bits in all T lanes).  Consecutive entries of a column name atoms close
-// together in slot order, so the 32 gathers of one instruction (32/T atoms, T consecutive entries
-// each) touch fewer 128-byte lines than 32 atoms' m-th entries do.  The force of the atom in slot
-// base + L ends in lane L, which then integrates it as the one-lane-per-atom kernel does.
-// cnt: the neighbour count of slot base + lane (0 for slots past the replica's atoms).
-template <int NB, int T>
-__device__ __forceinline__ AccF force_f32_tpa(const Arrays& A, const Scal& S, const Rep& R,
-                                              const float4* __restrict__ pos, int64_t base, int cnt)
-{
-    constexpr int G = 32 / T;                                 // atoms per pass
-    const int lane = threadIdx.x & 31;
-    const int t = lane % T, g = lane / T;
-    const int64_t ns = S.nslots;
-    AccF out{0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int p = 0; p < T; ++p) {
-        const int ia = p * G + g;                             // the atom of this lane's group
-        const int c = __shfl_sync(0xffffffffu, cnt, ia);
-        const int64_t slot = base + ia;
-        const int mm = min(c, S.cap);
-        const int mine = (mm > t) ? (mm - t + T - 1) / T : 0;
-        const float4 pi = (mm > 0) ? __ldg(pos + slot) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const uint32_t* __restrict__ Wc = A.W + int64_t(t) * ns + slot;
-        const int64_t step = int64_t(T) * ns;
-        AccF a = pair_loop_f32<NB>(S, R, pi, mine, [=](int k) { return __ldcs(Wc + int64_t(k) * step); },
-                                   [=](uint32_t e) { return __ldg(pos + (e >> IDX_SHIFT)); });
-#pragma unroll
-        for (int o = 1; o < T; o <<= 1) {
-            a.fx += __shfl_xor_sync(0xffffffffu, a.fx, o);
-            a.fy += __shfl_xor_sync(0xffffffffu, a.fy, o);
-            a.fz += __shfl_xor_sync(0xffffffffu, a.fz, o);
-            a.u += __shfl_xor_sync(0xffffffffu, a.u, o);
-            a.w += __shfl_xor_sync(0xffffffffu, a.w, o);
-        }
-        // lane L holds atom L after pass L / G, from the first lane of group L % G
-        const int src = (lane % G) * T;
-        const float fx = __shfl_sync(0xffffffffu, a.fx, src), fy = __shfl_sync(0xffffffffu, a.fy, src);
-        const float fz = __shfl_sync(0xffffffffu, a.fz, src), u = __shfl_sync(0xffffffffu, a.u, src);
-        const float w = __shfl_sync(0xffffffffu, a.w, src);
-        if (lane / G == p) out = AccF{fx, fy, fz, u, w};
-    }
-    return out;
-}
-
 // Two pairs (lanes x and y) of the FP32 pair loop: g(r^2) with the in-range masks, accumulated
 // into f (sum g (x_j - x_i)), u_i and the virial.
 __device__ __forceinline__ void pair2(const Scal& S, float2 dx, float2 dy, float2 dz, bool in0, bool in1,
@@ -200,7 +170,7 @@ __device__ __forceinline__ void pair2(const Scal& S, float2 dx, float2 dy, float
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
     in0 = in0 && r2.x < S.rc2f;
     in1 = in1 && r2.y < S.rc2f;
-    const float2 ri2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    const float2 ri2 = rcp2_nr(r2);
     const float2 sr2 = __fmul2_rn(sig2, ri2);
     const float2 sr6 = __fmul2_rn(__fmul2_rn(sr2, sr2), sr2);
     float2 fs = __fmul2_rn(__fmul2_rn(__fmul2_rn(eps48, sr6), __fadd2_rn(sr6, make_float2(-0.5f, -0.5f))), ri2);
@@ -306,7 +276,7 @@ __global__ void __launch_bounds__(TILE) k_half_pairs(Arrays A, Scal S, int cur)
                 const float dz = fmaf(offz_raw(e[k]) - 8388624.0f, wz16, pj[k].z - pi.z);
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (m0 + k < mm && r2 < S.rc2f) {
-                    const float ri2 = rcp_approx(r2);
+                    const float ri2 = rcp_nr(r2);
                     const float sr2 = S.sig2f * ri2;
                     const float sr6 = sr2 * sr2 * sr2;
                     const float fs = S.eps48f * sr6 * (sr6 - 0.5f) * ri2;     // g(r^2)
@@ -1095,12 +1065,10 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
 
 // SRC: where the forces come from -- 0 the neighbour matrix W, 1 the 27 cells (step kernel 4),
 // 2 the half-list buffers filled by k_half_pairs (step kernel 5; read and cleared here)
-// TPA: lanes per atom in the pair loop (force_f32_tpa; SRC 0 only)
-template <int MODE, bool PROPS, int NB, int MINB, int SRC = 0, int TPA = 1>
+template <int MODE, bool PROPS, int NB, int MINB, int SRC = 0>
 __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cur, cudaGraphConditionalHandle cond,
                                                       int use_cond)
 {
-    static_assert(TPA == 1 || SRC == 0, "lanes per atom > 1 read the neighbour matrix");
     static_assert(MODE != MD_FP64, "MD_FP64 steps run k_step");
     const int nxt = cur ^ 1;
     const int lane = threadIdx.x & 31;
@@ -1199,14 +1167,10 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         float part[NPROP];
 #pragma unroll
         for (int q = 0; q < NPROP; ++q) part[q] = 0.0f;
-        AccF a_tpa;
-        if (TPA > 1) a_tpa = force_f32_tpa<NB, TPA>(A, S, R, pos, int64_t(w0) * 32, active ? c0 : 0);
         if (active) {
             const float4 pi = __ldg(pos + slot);
             AccF a;
-            if (TPA > 1) {
-                a = a_tpa;
-            } else if (SRC == 1) {
+            if (SRC == 1) {
                 a = force_f32_cells(A, S, R, pos, slot, pi);
             } else if (SRC == 2) {
                 const float4 fb = __ldcs(A.fbuf + slot);
@@ -1792,35 +1756,6 @@ static int occ_src()
     return std::max(1, std::min(a, b));
 }
 
-template <int M, int NB, int MINB, int TPA>
-static int occ_tpa()
-{
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_step_sm<M, false, NB, MINB, 0, TPA>, TILE, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_sm<M, true, NB, MINB, 0, TPA>, TILE, 0);
-    return std::max(1, std::min(a, b));
-}
-
-// step kernel 1 with 2 or 4 lanes per atom: entries per batch 2 or 4 (8 maps to 4)
-#define GBMD_DISPATCH_TPA(M, FN)                                                          \
-    {                                                                                     \
-        const int mb = minb_of(L.ctas_req);                                               \
-        const bool nb4 = L.nbr_batch >= 4;                                                \
-        if (L.atom_threads >= 4) {                                                        \
-            if (nb4) {                                                                    \
-                if (mb == 16) FN(M, 4, 16, 4) else if (mb == 12) FN(M, 4, 12, 4) else if (mb == 8) FN(M, 4, 8, 4) else FN(M, 4, 4, 4) \
-            } else {                                                                      \
-                if (mb == 16) FN(M, 2, 16, 4) else if (mb == 12) FN(M, 2, 12, 4) else if (mb == 8) FN(M, 2, 8, 4) else FN(M, 2, 4, 4) \
-            }                                                                             \
-        } else {                                                                          \
-            if (nb4) {                                                                    \
-                if (mb == 16) FN(M, 4, 16, 2) else if (mb == 12) FN(M, 4, 12, 2) else if (mb == 8) FN(M, 4, 8, 2) else FN(M, 4, 4, 2) \
-            } else {                                                                      \
-                if (mb == 16) FN(M, 2, 16, 2) else if (mb == 12) FN(M, 2, 12, 2) else if (mb == 8) FN(M, 2, 8, 2) else FN(M, 2, 4, 2) \
-            }                                                                             \
-        }                                                                                 \
-    }
-
 template <int M, int SRC>
 static int occ_src_mb(int mb)
 {
@@ -1836,13 +1771,6 @@ int step_ctas_per_sm(const Scal& S, const Launch& L)
         const int mb = minb_of(L.ctas_req);
         if (L.step_kernel == 4) return S.mode == MD_MIXED ? occ_src_mb<MD_MIXED, 1>(mb) : occ_src_mb<MD_FP32, 1>(mb);
         return S.mode == MD_MIXED ? occ_src_mb<MD_MIXED, 2>(mb) : occ_src_mb<MD_FP32, 2>(mb);
-    }
-    if (L.step_kernel == 1 && L.atom_threads > 1) {
-#define GBMD_OCC(M, NB, MB, T) { occ = occ_tpa<M, NB, MB, T>(); }
-        if (S.mode == MD_MIXED) GBMD_DISPATCH_TPA(MD_MIXED, GBMD_OCC)
-        else GBMD_DISPATCH_TPA(MD_FP32, GBMD_OCC)
-#undef GBMD_OCC
-        return occ;
     }
     if (L.step_kernel == 3) {
 #define GBMD_OCC(M, NB, MB) { occ = occ_staged<M, NB, MB>(L.stage_smem); }
@@ -1926,16 +1854,6 @@ cudaError_t launch_step(const Arrays& A, const Scal& S, const Launch& L, int cur
         if (S.mode == MD_FP64) {
             if (props) k_step<MD_FP64, true, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);
             else k_step<MD_FP64, false, 2, 4, false><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond, 0);
-        }
-        else if (L.atom_threads > 1) {
-#define GBMD_STEP_TPA(M, NB, MB, T)                                                                           \
-    {                                                                                                          \
-        if (props) k_step_sm<M, true, NB, MB, 0, T><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);   \
-        else k_step_sm<M, false, NB, MB, 0, T><<<g, TILE, 0, L.stream>>>(A, S, cur, L.cond, L.use_cond);         \
-    }
-            if (S.mode == MD_MIXED) GBMD_DISPATCH_TPA(MD_MIXED, GBMD_STEP_TPA)
-            else GBMD_DISPATCH_TPA(MD_FP32, GBMD_STEP_TPA)
-#undef GBMD_STEP_TPA
         }
         else if (S.mode == MD_MIXED) GBMD_DISPATCH_NB_MINB(MD_MIXED, GBMD_STEP)
         else GBMD_DISPATCH_NB_MINB(MD_FP32, GBMD_STEP)

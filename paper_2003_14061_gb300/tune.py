@@ -9,12 +9,18 @@ arithmetic in the same order; the list-free step kernel (4) and the sub-cell bui
 force in another order, and the half-list kernel (5) adds through atomics in no fixed order, so
 choosing them changes the trajectory at the rounding level only.
 
-Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch, atom_threads) for the step
--- the per-thread kernel at register-bound residencies with 1, 2 or 4 lanes per atom, the list-free
-and half-list kernels, and on request the shared-memory ring and the staged-neighbour kernel (2
-and 3, slower on every measured workload) at the residencies their shared memory allows -- then
-build_batch and build_stage for the neighbour build (timed over steps that include rebuilds).
-Results are cached per GPU and workload signature in a JSON file.
+Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch) for the step -- the
+per-thread kernel at register-bound residencies, the list-free and half-list kernels, and on
+request the shared-memory ring and the staged-neighbour kernel (2 and 3, slower on every measured
+workload) at the residencies their shared memory allows -- then build_batch and build_stage for
+the neighbour build.
+
+Measurement: each candidate runs with direct launches and the library's per-phase CUDA events,
+and is scored as (step-phase ms per step) + (rebuild-phase ms per rebuild) x (rebuilds per step
+over the whole search).  Timing whole steps instead would let the number of rebuilds that fall in
+a trial (one rebuild of the 16.4M-atom LJ fluid costs as much as ten steps) decide between shapes
+a few per cent apart.  The chosen shape is then used with graphs as before.  Results are cached
+per GPU and workload signature in a JSON file.
 """
 from __future__ import annotations
 
@@ -31,8 +37,7 @@ CTAS_RING = (2, 3, 4, 6)       # shared-memory ring step kernel (shared-memory-b
 CTAS_STAGED = (4, 6, 8)        # staged-neighbour step kernel (register- and shared-memory-bound)
 CTAS_CELLS = (4, 8, 12)        # list-free and half-list step kernels (register-bound residency)
 NBR_BATCH = (2, 4, 8)
-NBR_BATCH_TPA = (2, 4)         # with 2 or 4 lanes per atom
-ATOM_THREADS = (2, 4)
+REBUILD_PHASES = ("bin", "reorder", "build")
 BUILD_BATCH = (1, 2, 4, 32)
 BUILD_STAGE = (2, 1)           # the build writes W entry by entry, or rows from shared memory
 
@@ -44,15 +49,32 @@ def signature(system) -> str:
             f"rho{system.n / float((system.boxes.prod(axis=1)).sum()):.3f}")
 
 
-def _time_steps(system, steps: int) -> float:
-    s = system.stream
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
+def _rebuilds(system) -> int:
+    return sum(int(p["rebuilds"]) for p in system.props())
+
+
+class _Rate:
+    """Rebuilds per step over every trial so far (the same physical system throughout)."""
+    steps = 0
+    rebuilds = 0
+
+
+def _time_steps(system, steps: int, rate: _Rate = None) -> float:
+    """Score of the current launch shape in ms per step (see the module docstring)."""
+    r0 = _rebuilds(system)
+    system.set_timing(True)
     system.integrate(steps)
-    e1.record(s)
-    e1.synchronize()
-    return e0.elapsed_time(e1) / steps
+    ph = system.timing()
+    system.set_timing(False)
+    k = _rebuilds(system) - r0
+    step_ms = ph["step"][0] / steps
+    rebuild_ms = sum(ph[name][0] for name in REBUILD_PHASES)
+    if rate is None:
+        return step_ms + rebuild_ms / steps
+    rate.steps += steps
+    rate.rebuilds += k
+    per_step = rate.rebuilds / rate.steps
+    return step_ms + (rebuild_ms / k * per_step if k else rebuild_ms / steps)
 
 
 def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False,
@@ -75,31 +97,26 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
     steps = max(32, (steps // 16) * 16)           # whole 16-step graph replays
     trials = {}
 
+    rate = _Rate()
+    use_graph = system.tuning()["use_graph"]
+
     def trial(**kw):
-        system.set_tuning(**kw)
-        system.integrate(16)                       # capture the graph outside the timing
-        ms = _time_steps(system, steps)
+        system.set_tuning(use_graph=2, **kw)
+        system.integrate(16)                       # first launches outside the timing
+        ms = _time_steps(system, steps, rate)
         trials[json.dumps(kw, sort_keys=True)] = ms
         if verbose:
             print(f"tune {kw}: {ms * 1e3:.1f} us/step", flush=True)
         return ms
 
     cur = system.tuning()
-    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage",
-                                "atom_threads")}
+    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage")}
     best_ms = trial(**best)
-    fp64 = system.params.precision == B.MD_FP64
-    kernels = (1,) if fp64 else tuple(step_kernels)
-    shapes = []                                    # (step kernel, lanes per atom, residencies, batches)
+    kernels = (1,) if system.params.precision == B.MD_FP64 else tuple(step_kernels)
     for sk in kernels:
-        ctas = {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS, 5: CTAS_CELLS}[sk]
-        shapes.append((sk, 1, ctas, NBR_BATCH if sk < 4 else (2,)))
-        if sk == 1 and not fp64:
-            shapes += [(1, t, CTAS, NBR_BATCH_TPA) for t in ATOM_THREADS]
-    for sk, tpa, ctas_set, nbs in shapes:
-        for ctas in ctas_set:
-            for nb in nbs:
-                cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk, atom_threads=tpa)
+        for ctas in {1: CTAS, 2: CTAS_RING, 3: CTAS_STAGED, 4: CTAS_CELLS, 5: CTAS_CELLS}[sk]:
+            for nb in (NBR_BATCH if sk < 4 else (2,)):
+                cand = dict(best, ctas_per_sm=ctas, nbr_batch=nb, step_kernel=sk)
                 if json.dumps(cand, sort_keys=True) in trials:
                     continue
                 ms = trial(**cand)
@@ -113,7 +130,7 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
             ms = trial(**cand)
             if ms < best_ms:
                 best, best_ms = cand, ms
-    system.set_tuning(**best)
+    system.set_tuning(use_graph=use_graph, **best)
     result = {"best": best, "ms_per_step": best_ms, "trials": trials, "signature": key,
               "seconds": time.perf_counter() - t_start}
     if cache:

@@ -450,9 +450,9 @@ def test_small_workspace_is_rejected():
 FULL = {
     "wca_4M": dict(ncell=100, rho=0.8, rc=WCA_RC, skin=0.4, T=1.0, steps=20),
     "lj_16M": dict(ncell=160, rho=0.8442, rc=2.5, skin=0.3, T=0.72, steps=8),
-    # 4 lanes per atom in the pair loop, the props reduced in every step
-    "lj_16M_lanes4": dict(ncell=160, rho=0.8442, rc=2.5, skin=0.3, T=0.72, steps=8, props_every=1,
-                          tuning=dict(atom_threads=4, nbr_batch=4, ctas_per_sm=12)),
+    # the props reduced in every step (fixed-point sums in the step kernel), another launch shape
+    "lj_16M_props": dict(ncell=160, rho=0.8442, rc=2.5, skin=0.3, T=0.72, steps=8, props_every=1,
+                         tuning=dict(nbr_batch=2, ctas_per_sm=8)),
 }
 
 
@@ -499,55 +499,6 @@ def test_full_size_sampled(name):
         assert np.array_equal(ser[:, 0], np.arange(c["steps"]))
         k = c["steps"]
         assert np.abs((ser[:, 1] + ser[:, 2]) - (po[:k, 0] + po[:k, 1])).max() / n <= 1e-6
-
-
-# ---------------------------------------------------------------------------------------------
-# step kernel 1 with 2 or 4 lanes per atom in the pair loop
-# ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("nb", [2, 4])
-@pytest.mark.parametrize("lanes", [2, 4])
-@pytest.mark.parametrize("prec", ["mixed", "fp32"])
-@pytest.mark.parametrize("name", ["wca1372", "lj1372"])
-def test_lanes_per_atom_match_oracle(name, prec, lanes, nb):
-    # 1372 atoms: 11 tiles, the last one ragged (the lanes of slots past the atoms join the
-    # shuffles with no neighbours)
-    s, x, v, box, rc, skin = make(name, prec, props_every=1)
-    s.set_tuning(atom_threads=lanes, nbr_batch=nb, ctas_per_sm=8)
-    s.integrate(100)
-    xg, vg, _ = s.state()
-    ser = s.series(128)[0]
-    pr = s.props()[0]
-    p = oracle.pot(rc=rc)
-    xo, vo, po, rb = oracle.run(x, v, box, p, dt=0.005, nsteps=100, rule=1, skin=skin)
-    n = x.shape[0]
-    assert np.abs(min_image(xg - xo, box)).max() <= 1e-4
-    assert rel_l2(vg, vo) <= 1e-4
-    assert abs(pr["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / n) <= 1e-6
-    assert np.abs((ser[:, 1] + ser[:, 2]) - (po[:100, 0] + po[:100, 1])).max() / n <= 1e-6
-    assert abs(pr["rebuilds"] - (rb + 1)) <= 2
-
-
-def test_lanes_per_atom_batched_replicas():
-    specs = inputs.replica_specs(6, 300, 3000, 0.6, 0.9, seed=31)
-    states = [(inputs.perturb(xr, br, 0.08, 90 + r), vr, br)
-              for r, (xr, vr, br) in enumerate(inputs.replica_states(specs, 1.0, seed=31))]
-    n_rep = [sp[0] for sp in specs]
-    x = np.concatenate([st[0] for st in states])
-    v = np.concatenate([st[1] for st in states])
-    s = MDSystem(x, v, n_rep=n_rep, boxes=np.stack([st[2] for st in states]), rc=WCA_RC, skin=0.4,
-                 precision="mixed", props_every=1)
-    s.set_tuning(atom_threads=4, nbr_batch=4)
-    s.integrate(50)
-    xg, vg, _ = s.state()
-    ser = s.series(64)
-    off = 0
-    for r, (xr, vr, br) in enumerate(states):
-        n = xr.shape[0]
-        xo, vo, po, _ = oracle.run(xr, vr, br, oracle.pot(), dt=0.005, nsteps=50)
-        assert np.abs(min_image(xg[off:off + n] - xo, br)).max() <= 1e-4
-        assert rel_l2(vg[off:off + n], vo) <= 1e-4
-        assert np.abs((ser[r, :, 1] + ser[r, :, 2]) - (po[:50, 0] + po[:50, 1])).max() / n <= 1e-6
-        off += n
 
 
 # ---------------------------------------------------------------------------------------------

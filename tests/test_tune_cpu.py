@@ -17,7 +17,7 @@ class FakeSystem:
     def __init__(self, precision=B.MD_MIXED):
         self.params = FakeParams(precision)
         self.t = {"ctas_per_sm": 8, "nbr_batch": 2, "build_batch": 2, "use_graph": 1, "step_kernel": 1,
-                  "build_stage": 2, "atom_threads": 1}
+                  "build_stage": 2}
         self.set_calls = []
         self.steps = 0
 
@@ -33,44 +33,40 @@ class FakeSystem:
 
 
 def cost(t):
-    # a unique minimum at step kernel 1 with 2 lanes per atom, 12 CTAs/SM, 4 entries per batch,
-    # build batch 4
+    # a unique minimum at step kernel 1, 12 CTAs/SM, 4 entries per batch, build batch 4
     c = 1.0 + 0.1 * abs(t["ctas_per_sm"] - 12) + 0.05 * abs(t["nbr_batch"] - 4)
     c += {1: 0.0, 2: 0.5, 3: 0.7, 4: 0.9, 5: 0.6}[t["step_kernel"]] + {1: 0.1, 2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
-    c += {1: 0.0, 2: 0.01}[t["build_stage"]] + {1: 0.03, 2: 0.0, 4: 0.02}[t["atom_threads"]]
+    c += {1: 0.0, 2: 0.01}[t["build_stage"]]
     return c
 
 
 @pytest.fixture
 def fake_timing(monkeypatch):
-    monkeypatch.setattr(tune, "_time_steps", lambda system, steps: cost(system.tuning()))
+    monkeypatch.setattr(tune, "_time_steps", lambda system, steps, rate=None: cost(system.tuning()))
     monkeypatch.setattr(tune, "signature", lambda system: f"fake|prec{system.params.precision}")
 
 
 def test_search_finds_the_fastest_shape(fake_timing):
     s = FakeSystem()
     res = tune.tune(s, steps=64)
-    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1, "build_stage": 1,
-                           "atom_threads": 2}
+    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1, "build_stage": 1}
     assert res["ms_per_step"] == pytest.approx(1.0)
     assert res["ms_per_step"] == min(res["trials"].values())
     tried = [json.loads(k) for k in res["trials"]]
     assert {t["step_kernel"] for t in tried} == {1, 4, 5}            # 2 and 3 only on request
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 1} == set(tune.CTAS)
-    assert {t["atom_threads"] for t in tried if t["step_kernel"] == 1} == {1, 2, 4}
-    assert {t["nbr_batch"] for t in tried if t["atom_threads"] > 1} == set(tune.NBR_BATCH_TPA)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 4} == set(tune.CTAS_CELLS)
     assert {t["ctas_per_sm"] for t in tried if t["step_kernel"] == 5} == set(tune.CTAS_CELLS)
     assert {t["nbr_batch"] for t in tried if t["step_kernel"] in (4, 5)} == {2}
     assert {t["build_batch"] for t in tried} == set(tune.BUILD_BATCH)
     assert s.tuning()["ctas_per_sm"] == 12 and s.tuning()["build_batch"] == 4
+    assert s.tuning()["use_graph"] == 1                # trials run direct launches; graphs come back
     assert s.steps % 16 == 0                       # whole 16-step graph replays only
 
 
 def test_fp64_searches_the_per_thread_kernel_only(fake_timing):
     res = tune.tune(FakeSystem(B.MD_FP64), steps=32)
     assert {json.loads(k)["step_kernel"] for k in res["trials"]} == {1}
-    assert {json.loads(k)["atom_threads"] for k in res["trials"]} == {1}
 
 
 def test_step_kernels_can_be_restricted(fake_timing):
