@@ -54,13 +54,15 @@ def combine_ranks(ms: float, atoms: int, steps: int, device=None):
     return ms_max, total, total * steps / (ms_max * 1e-3)
 
 
-def code_hash(path: str) -> str:
-    """sha256 (16 hex digits) of a C/CUDA source with comments and whitespace removed, so that
-    only code changes invalidate a capture taken on it."""
+def code_hash(paths) -> str:
+    """sha256 (16 hex digits) of C/CUDA sources (one path or a list) with comments and whitespace
+    removed, so that only code changes invalidate a capture taken on them."""
     import hashlib
     import re
-    with open(path) as f:
-        src = f.read()
+    src = ""
+    for path in ([paths] if isinstance(paths, str) else paths):
+        with open(path) as f:
+            src += f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
     src = re.sub(r"\s+", "", src)
@@ -72,7 +74,8 @@ def traffic_per_atom(kernel: str):
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)[kernel]
-        sha = code_hash(os.path.join(ROOT, rec["source"]))
+        src = rec["source"]
+        sha = code_hash([os.path.join(ROOT, p) for p in ([src] if isinstance(src, str) else src)])
         return float(rec["dram_bytes_per_atom"]) if sha == rec["code_sha256_16"] else None
     except (OSError, KeyError, ValueError):
         return None
@@ -348,6 +351,8 @@ def run_gb300(args, rank, world, local_rank):
     s.set_timing(False)
     s.set_tuning(use_graph=2 if args.no_graph else 1)
     step_ms, step_calls, step_launches = phases["step"]
+    # with the props in every step, every timed launch is the step kernel's props form
+    roof_kernel = "k_step_sm<MD_MIXED, props>" if args.props_every == 1 else "k_step_sm<MD_MIXED>"
     peak, peak_kind = load_peaks()
     bpa = algorithmic_bytes_per_atom_step(mean_nbrs, "mixed", RULE)
     per_launch_ms = step_ms / max(step_calls, 1)
@@ -432,8 +437,8 @@ def run_gb300(args, rank, world, local_rank):
                                       "are the forms wca4m_mixed_props1/_props10 and the e2e loop")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (lambda b: None if b is None else b * n)(traffic_per_atom("k_step_sm<MD_MIXED>")),
-                         "kernel": "k_step_sm<MD_MIXED>",
+                         "traffic": (lambda b: None if b is None else b * n)(traffic_per_atom(roof_kernel)),
+                         "kernel": roof_kernel,
                          "bytes_per_atom": bpa, "peak_kind": peak_kind},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 48.0 * total_atoms / e2e_steps,

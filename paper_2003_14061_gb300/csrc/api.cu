@@ -110,6 +110,7 @@ int make_plan(const md_params* p, int32_t nrep, const int64_t* n_rep, const doub
             R.w[a] = L / double(R.nc[a]);
             R.s[a] = double(R.nc[a]) / L;
             R.wf[a] = float(R.w[a]);
+            R.wlo[a] = float(R.w[a] - double(R.wf[a]));
             nc_tot *= R.nc[a];
         }
         R.kz = p->cell_block > 0 ? pow2_floor(std::min(p->cell_block, R.nc[2])) : 0;   // 0: chosen in md_create

@@ -53,7 +53,10 @@ struct Rep {                  // per replica, fixed after creation
     double w[3];              // cell sides L / n_c
     double s[3];              // n_c / L
     float wf[3];              // (float) w
-    float pad2;
+    float wlo[3];             // (float) (w - wf): the FP32 pair displacement adds o wf, then o wlo,
+                              // so that the rounding of w does not bias every cross-cell distance
+                              // of an axis the same way
+    float pad2[2];
 };
 
 struct RepState {             // per replica, mutable on the device
@@ -261,64 +264,13 @@ __device__ __forceinline__ uint32_t cell_bits(double w) { return uint32_t(__doub
 __device__ __forceinline__ float cell_word_f(uint32_t p) { return __uint_as_float(p); }
 __device__ __forceinline__ double cell_word_d(uint32_t p) { return double(p); }
 
-// FP32 <-> FP64 conversions on the integer pipe.  On GB300 the F2F conversions issue to the FP64
-// pipe, which runs at 1/64 of the FP32 rate and is the bound of a step that also reduces the
-// FP64 props; these versions edit the IEEE-754 fields with 32-bit integer operations instead and
-// return exactly what the hardware conversions return (round to nearest even, subnormals,
-// infinities, quieted NaNs).
-__device__ __forceinline__ double f32_to_f64(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t sgn = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x007FFFFFu;
-    uint32_t hi, lo;
-    if (e != 0u && e != 0xFFu) {                 // normal: rebias 127 -> 1023, widen the fraction
-        hi = sgn | ((e + 896u) << 20) | (m >> 3);
-        lo = m << 29;
-    } else if (e == 0xFFu) {                     // inf, or NaN with its quiet bit set
-        hi = sgn | 0x7FF00000u | (m >> 3) | (m ? 0x00080000u : 0u);
-        lo = m << 29;
-    } else if (m == 0u) {                        // signed zero
-        hi = sgn;
-        lo = 0u;
-    } else {                                     // subnormal m 2^-149 = 1.f 2^(p-149), p its top bit
-        const int p = 31 - __clz(int(m));
-        const uint32_t frac = m ^ (1u << p);     // p leading fraction bits, moved to the top of 52
-        const int sh = 52 - p;                   // 30..52
-        hi = sgn | (uint32_t(p + 874) << 20) | (sh >= 32 ? (frac << (sh - 32)) : (frac >> (32 - sh)));
-        lo = sh >= 32 ? 0u : (frac << sh);
-    }
-    return __hiloint2double(int(hi), int(lo));
-}
-
-__device__ __forceinline__ float f64_to_f32(double x)
-{
-    const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
-    const uint32_t sgn = hi & 0x80000000u;
-    const int E = int((hi >> 20) & 0x7FFu);
-    const int e = E - 896;                       // float exponent field if the result is normal
-    if (E == 0x7FF) {                            // inf, or NaN keeping its top 22 payload bits, quieted
-        const uint32_t m = ((hi & 0x000FFFFFu) << 3) | (lo >> 29);
-        const bool nan = ((hi & 0x000FFFFFu) | lo) != 0u;
-        return __uint_as_float(sgn | 0x7F800000u | (nan ? (m | 0x00400000u) : 0u));
-    }
-    if (e >= 255) return __uint_as_float(sgn | 0x7F800000u);               // overflow
-    if (e >= 1) {                                // normal result: 29 bits dropped, carry may reach inf
-        uint32_t mag = (uint32_t(e) << 23) | ((hi & 0x000FFFFFu) << 3) | (lo >> 29);
-        const uint32_t rem = lo & 0x1FFFFFFFu;
-        mag += (rem > 0x10000000u || (rem == 0x10000000u && (mag & 1u))) ? 1u : 0u;
-        return __uint_as_float(sgn | mag);
-    }
-    if (E == 0) return __uint_as_float(sgn);     // double zero or subnormal: below half the least float
-    // subnormal (or zero) result: m = round(1.f 2^(E-1023) 2^149) = round(M >> (926 - E)), M the
-    // 53-bit significand; a carry to 2^23 gives the least normal float, as it should
-    const int sh = 926 - E;                      // >= 30
-    if (sh >= 54) return __uint_as_float(sgn);   // below half the least subnormal
-    const uint64_t M = (uint64_t((hi & 0x000FFFFFu) | 0x00100000u) << 32) | lo;
-    uint32_t mq = uint32_t(M >> sh);
-    const uint64_t rem = M & ((uint64_t(1) << sh) - 1u), half = uint64_t(1) << (sh - 1);
-    mq += (rem > half || (rem == half && (mq & 1u))) ? 1u : 0u;
-    return __uint_as_float(sgn | mq);
-}
+// FP32 <-> FP64 conversions (round to nearest even).  The hardware conversions issue to the FP64
+// pipe (1/64 of the FP32 rate on GB300); versions that edit the IEEE-754 fields with 32-bit
+// integer operations returned the same bits but made the step kernel 3.5 % slower (more issue
+// slots for fewer FP64-pipe cycles, the FP64 pipe not being the bound), so these are the
+// hardware ones.
+__device__ __forceinline__ double f32_to_f64(float f) { return double(f); }
+__device__ __forceinline__ float f64_to_f32(double x) { return __double2float_rn(x); }
 
 // Warp-wide sums and maxima.
 __device__ __forceinline__ double warp_sum(double x)

@@ -35,7 +35,7 @@ __device__ __forceinline__ float offz16_a(uint32_t e) { return __uint_as_float(0
 // mu = kappa lh of this step (written by the previous step or by the permute into slot order),
 // so a neighbour costs one FP64 3-vector gather; this step writes mu[out_buf] = kappa_next lh'
 // for the next one.  The neighbour loop runs NB entries at a time: their W rows, positions and mu
-// are loaded together.  FP32<->FP64 conversions run on the integer pipe (exact).
+// are loaded together.
 constexpr int ADJ_NB = 4;
 
 __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView V, int q, double kappa, double w_U,
@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView 
             float u = 0.f, us = 0.f;
             const int mm = min(cnt[slot], S.cap);
             const float wx = R.wf[0], wy4 = 0.25f * R.wf[1], wz16 = 0.0625f * R.wf[2];
+            const float wxl = R.wlo[0], wy4l = 0.25f * R.wlo[1], wz16l = 0.0625f * R.wlo[2];
             for (int m0 = 0; m0 < mm; m0 += ADJ_NB) {
                 uint32_t e[ADJ_NB];
                 float4 pj[ADJ_NB];
@@ -83,9 +84,10 @@ __global__ void __launch_bounds__(TILE) k_adj_reverse(Arrays A, Scal S, AdjView 
 #pragma unroll
                 for (int k = 0; k < ADJ_NB; ++k) {
                     const uint32_t ek = e[k];
-                    const float dx = fmaf(offx_a(ek), wx, pj[k].x - pi.x);      // d = x_j - x_i
-                    const float dy = fmaf(offy4_a(ek), wy4, pj[k].y - pi.y);
-                    const float dz = fmaf(offz16_a(ek), wz16, pj[k].z - pi.z);
+                    const float ox = offx_a(ek), oy = offy4_a(ek), oz = offz16_a(ek);
+                    const float dx = fmaf(ox, wxl, fmaf(ox, wx, pj[k].x - pi.x));      // d = x_j - x_i
+                    const float dy = fmaf(oy, wy4l, fmaf(oy, wy4, pj[k].y - pi.y));
+                    const float dz = fmaf(oz, wz16l, fmaf(oz, wz16, pj[k].z - pi.z));
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (m0 + k < mm && r2 < S.rc2f) {
                         const float ri2 = 1.0f / r2;

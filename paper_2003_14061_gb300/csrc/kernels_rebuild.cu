@@ -10,9 +10,7 @@
 //   k_sort_cells   the atomic layer order is indeterminate (Sec. 2.3 notes the resulting
 //                  irreproducibility); sorting each cell's slots makes the order, and every
 //                  result after it, deterministic.  It also writes psort, the FP32 positions in
-//                  that order with each slot in .w, which the FP32 builds read; for them each
-//                  cell is ordered by cell-local x (then slot), so that a row of three cells is
-//                  sorted along x and the build can test only the x-window within reach.
+//                  that order with each slot in .w, which the FP32 builds read.
 //   k_reorder_*    Sec. 4.1 item 1: permute the atoms into cell order (gather through scratch).
 //   k_build_sorted N5 in FP32: W from the 27 neighbouring cells, one thread per atom, each row of
 //                  3 cells read as a contiguous run of psort; W stored row-major for coalescing
@@ -401,22 +399,6 @@ __global__ void __launch_bounds__(256) k_sort_cells(Arrays A, Scal S, int cur)
                 const float4 p = pos[j];
                 A.psort[k] = make_float4(p.x, p.y, p.z, __int_as_float(j));
             }
-            if (S.mode != MD_FP64) {
-                // FP32 builds: each cell in ascending cell-local x, equal x in ascending slot (a
-                // stable insertion sort of the slot order), perm to match.  A row of three cells
-                // is then in ascending x + o_x w, and the build tests only the x-window of it
-                // that can lie within r_c + skin.
-                for (int k = b + 1; k < e; ++k) {
-                    const float4 key = A.psort[k];
-                    int q = k - 1;
-                    while (q >= b && A.psort[q].x > key.x) {
-                        A.psort[q + 1] = A.psort[q];
-                        --q;
-                    }
-                    A.psort[q + 1] = key;
-                }
-                for (int k = b; k < e; ++k) A.perm[k] = __float_as_int(A.psort[k].w);
-            }
         }
     }
 }
@@ -680,38 +662,12 @@ __device__ __forceinline__ void nbr_test(const float4& p, const float2& npxy, fl
     }
 }
 
-// The x-window of a row of three cells (FP32 builds).  Each cell of psort is in ascending
-// cell-local x, so the run [kb, ke) is in ascending g(k) = x_k + o_x w (o_x = -1, 0, 1 for the
-// cells [.., b1), [b1, b2), [b2, ..)).  A candidate within r_c + skin of the atom (cell-local x
-// xi) has |g - xi| <= sqrt(r2max) with r2max = (r_c + skin)^2 less the squared distance from
-// the atom to the row's cells in y and z; two binary searches narrow [kb, ke) to the candidates
-// with |g - xi| <= that bound plus a margin far above the rounding of g and of the criterion
-// (the margin of skip2 is 1e-5 relative).  The candidates dropped all fail the criterion, and the
-// order of those kept is unchanged, so W is the same entry for entry.
-constexpr int XWIN_MIN = 8;          // shorter runs are tested whole
-
-__device__ __forceinline__ void x_window(const float4* __restrict__ ps, int b1, int b2, float w, float xi,
-                                         float r2max, int& kb, int& ke)
-{
-    const float hw = sqrtf(fmaxf(r2max, 0.0f)) * 1.00001f + 1e-5f * w;
-    const float xlo = xi - hw, xhi = xi + hw;
-    auto g = [&](int k) { return __ldg(&ps[k].x) + ((k < b1) ? -w : ((k < b2) ? 0.0f : w)); };
-    int lo = kb, hi = ke;
-    while (lo < hi) {                // first k with g(k) >= xlo
-        const int mid = (lo + hi) >> 1;
-        if (g(mid) < xlo) lo = mid + 1;
-        else hi = mid;
-    }
-    int lo2 = lo;
-    hi = ke;
-    while (lo2 < hi) {               // first k with g(k) > xhi
-        const int mid = (lo2 + hi) >> 1;
-        if (g(mid) <= xhi) lo2 = mid + 1;
-        else hi = mid;
-    }
-    kb = lo;
-    ke = lo2;
-}
+// The order in which a CTA of a neighbour build takes the rebuild tiles: chunks of BUILD_CHUNK
+// consecutive tiles dealt to the CTAs in turn, so that the CTAs resident at one time work on one
+// stretch of consecutive slots (grid x BUILD_CHUNK tiles) and the candidate rows they read stay
+// in L2; contiguous runs per CTA spread them over the whole system (measured in the build A/B).
+constexpr int BUILD_CHUNK = 4;
+#define build_tile(q) ((((q) / BUILD_CHUNK) * int(gridDim.x) + int(blockIdx.x)) * BUILD_CHUNK + (q) % BUILD_CHUNK)
 
 // STAGE: a thread appends its column of W to shared memory (stride TILE) instead of W itself,
 // and each warp then writes its columns row by row: 32 consecutive slots of a row are 128
@@ -736,11 +692,11 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
     const float rl2 = S.rl2f;
     const float skip2 = rl2 * (1.0f + 1e-5f);
     const int nrb = A.g->n_rb_tiles;
-    const int per = (nrb + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(nrb, t_begin + per);
     int run_r = -1, run_max = 0;
     long long run_sum = 0;
-    for (int it = t_begin; it < t_end; ++it) {
+    for (int q = 0;; ++q) {
+        const int it = build_tile(q);
+        if (it >= nrb) break;
         const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
         if (r != run_r) {
@@ -782,9 +738,8 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
                     if (inner) {
                         // cells cx-1, cx, cx+1 are adjacent runs [b0,b1) [b1,b2) [b2,b3) of psort
                         const int b0 = cs[row + cx - 1], b1 = cs[row + cx], b2 = cs[row + cx + 1];
-                        int kb = use_l ? b0 : b1;
-                        int ke = use_r ? cs[row + cx + 2] : b2;
-                        if (ke - kb >= XWIN_MIN) x_window(ps, b1, b2, w0, pi.x, skip2 - dyz, kb, ke);
+                        const int kb = use_l ? b0 : b1;
+                        const int ke = use_r ? cs[row + cx + 2] : b2;
                         for (int k0 = kb; k0 < ke; k0 += BB) {
                             float4 pj[BB];
 #pragma unroll
@@ -933,11 +888,11 @@ __global__ void __launch_bounds__(TILE) k_build_sub(Arrays A, Scal S, int cur)
     const float rl2 = S.rl2f;
     const float skip2 = rl2 * (1.0f + 1e-5f);
     const int nrb = A.g->n_rb_tiles;
-    const int per = (nrb + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per, t_end = min(nrb, t_begin + per);
     int run_r = -1, run_max = 0;
     long long run_sum = 0;
-    for (int it = t_begin; it < t_end; ++it) {
+    for (int q = 0;; ++q) {
+        const int it = build_tile(q);
+        if (it >= nrb) break;
         const int t = A.rb_tiles[it];
         const int r = A.tile_rep[t];
         if (r != run_r) {
@@ -1080,11 +1035,12 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int per = (S.ncells + nw - 1) / nw;
-    const int c_begin = gw * per, c_end = min(S.ncells, c_begin + per);
     int run_r = -1, run_max = 0;
     long long run_sum = 0;
-    for (int c = c_begin; c < c_end; ++c) {
+    // cells in chunks of 2 dealt to the warps in turn (as build_tile does for tiles)
+    for (int q = 0;; ++q) {
+        const int c = ((q >> 1) * nw + gw) * 2 + (q & 1);
+        if (c >= S.ncells) break;
         const int r = A.cell_rep[c];
         if (r != run_r) {
             if (run_r >= 0) {

@@ -47,10 +47,9 @@ __device__ __forceinline__ float rcp_approx(float x)
 }
 
 // 1/r^2 for the pair terms: the approximation above refined by one Newton-Raphson step for the
-// reciprocal, y <- y + y (1 - x y), which leaves about half an ulp of error with no bias.  Without
-// it u(r) inherits the approximation's error several times over (r^-12 = (r^-2)^6), and summed
-// over millions of pairs of a dense fluid that came to 2.4e-6 per atom in the energy.  Lanes
-// whose r^2 is 0 (padding, masked afterwards) give NaN here, never used.
+// reciprocal, y <- y + y (1 - x y), which leaves about half an ulp of error with no bias (u(r)
+// takes the error of 1/r^2 six times over, r^-12 = (r^-2)^6, and the energy sums millions of
+// such terms).  Lanes whose r^2 is 0 (padding, masked afterwards) give NaN here, never used.
 __device__ __forceinline__ float2 rcp2_nr(float2 x)
 {
     const float2 y = make_float2(rcp_approx(x.x), rcp_approx(x.y));
@@ -95,6 +94,9 @@ __device__ __forceinline__ AccF pair_loop_f32(const Scal& S, const Rep& R, float
     const float2 wx = make_float2(R.wf[0], R.wf[0]);
     const float2 wy4 = make_float2(0.25f * R.wf[1], 0.25f * R.wf[1]);
     const float2 wz16 = make_float2(0.0625f * R.wf[2], 0.0625f * R.wf[2]);
+    const float2 wxl = make_float2(R.wlo[0], R.wlo[0]);
+    const float2 wy4l = make_float2(0.25f * R.wlo[1], 0.25f * R.wlo[1]);
+    const float2 wz16l = make_float2(0.0625f * R.wlo[2], 0.0625f * R.wlo[2]);
     const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
     const float2 sig2 = make_float2(S.sig2f, S.sig2f), eps48 = make_float2(S.eps48f, S.eps48f);
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, u = fx, w = fx;
@@ -114,9 +116,9 @@ __device__ __forceinline__ AccF pair_loop_f32(const Scal& S, const Rep& R, float
             const float2 ox = __fadd2_rn(make_float2(offx_raw(e0), offx_raw(e1)), make_float2(-8388609.0f, -8388609.0f));
             const float2 oy = __fadd2_rn(make_float2(offy_raw(e0), offy_raw(e1)), make_float2(-8388612.0f, -8388612.0f));
             const float2 oz = __fadd2_rn(make_float2(offz_raw(e0), offz_raw(e1)), make_float2(-8388624.0f, -8388624.0f));
-            const float2 dx = __ffma2_rn(ox, wx, __fadd2_rn(make_float2(pj[k].x, pj[k + 1].x), npx));
-            const float2 dy = __ffma2_rn(oy, wy4, __fadd2_rn(make_float2(pj[k].y, pj[k + 1].y), npy));
-            const float2 dz = __ffma2_rn(oz, wz16, __fadd2_rn(make_float2(pj[k].z, pj[k + 1].z), npz));
+            const float2 dx = __ffma2_rn(ox, wxl, __ffma2_rn(ox, wx, __fadd2_rn(make_float2(pj[k].x, pj[k + 1].x), npx)));
+            const float2 dy = __ffma2_rn(oy, wy4l, __ffma2_rn(oy, wy4, __fadd2_rn(make_float2(pj[k].y, pj[k + 1].y), npy)));
+            const float2 dz = __ffma2_rn(oz, wz16l, __ffma2_rn(oz, wz16, __fadd2_rn(make_float2(pj[k].z, pj[k + 1].z), npz)));
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const bool in0 = (m0 + k < mm) && r2.x < S.rc2f;
             const bool in1 = (m0 + k + 1 < mm) && r2.y < S.rc2f;
@@ -202,7 +204,7 @@ __device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, 
     const int2* __restrict__ ck = A.ckeep;                  // [start, end) of each cell in the replica
     const int64_t sbase = R.slot0;                          // slot of replica cell-order position k
     const int ncx = R.nc[0];
-    const float wx = R.wf[0];
+    const float wx = R.wf[0], wxl = R.wlo[0];
     const float2 npx = make_float2(-pi.x, -pi.x), npy = make_float2(-pi.y, -pi.y), npz = make_float2(-pi.z, -pi.z);
     float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx, u = fx, w = fx;
     const int xs[3] = {(cx == 0) ? ncx - 1 : cx - 1, cx, (cx == ncx - 1) ? 0 : cx + 1};
@@ -210,9 +212,11 @@ __device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, 
     for (int oz = -1; oz <= 1; ++oz) {
         int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
         const float2 offz = make_float2(float(oz) * R.wf[2], float(oz) * R.wf[2]);
+        const float2 offzl = make_float2(float(oz) * R.wlo[2], float(oz) * R.wlo[2]);
         for (int oy = -1; oy <= 1; ++oy) {
             int ny = cy + oy; ny += (ny < 0) ? R.nc[1] : 0; ny -= (ny >= R.nc[1]) ? R.nc[1] : 0;
             const float2 offy = make_float2(float(oy) * R.wf[1], float(oy) * R.wf[1]);
+            const float2 offyl = make_float2(float(oy) * R.wlo[1], float(oy) * R.wlo[1]);
             const int row = R.cell0 + row_pos(R, ny, nz) * ncx;
             // runs [b, e) with their x offsets: one run of three cells, or three at a wrap in x
             const int nrun = inner ? 1 : 3;
@@ -229,10 +233,11 @@ __device__ __forceinline__ AccF force_f32_cells(const Arrays& A, const Scal& S, 
                     // o_x of each candidate: the run's first cell, +1 past b1, +2 past b2
                     const float o0 = oq + float(k0 >= b1) + float(k0 >= b2);
                     const float o1 = oq + float(k1 >= b1) + float(k1 >= b2);
-                    const float2 dx = __ffma2_rn(make_float2(o0, o1), make_float2(wx, wx),
-                                                 __fadd2_rn(make_float2(p0.x, p1.x), npx));
-                    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(p0.y, p1.y), npy), offy);
-                    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(p0.z, p1.z), npz), offz);
+                    const float2 dx = __ffma2_rn(make_float2(o0, o1), make_float2(wxl, wxl),
+                                                 __ffma2_rn(make_float2(o0, o1), make_float2(wx, wx),
+                                                            __fadd2_rn(make_float2(p0.x, p1.x), npx)));
+                    const float2 dy = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(p0.y, p1.y), npy), offy), offyl);
+                    const float2 dz = __fadd2_rn(__fadd2_rn(__fadd2_rn(make_float2(p0.z, p1.z), npz), offz), offzl);
                     pair2(S, dx, dy, dz, j0 != slot, v1 && j1 != slot, fx, fy, fz, u, w);
                 }
             }
@@ -261,6 +266,7 @@ __global__ void __launch_bounds__(TILE) k_half_pairs(Arrays A, Scal S, int cur)
         const int mm = min(__ldcs(A.nbr_count + slot), S.cap);
         const uint32_t* __restrict__ Wc = A.W + slot;
         const float wx = R.wf[0], wy4 = 0.25f * R.wf[1], wz16 = 0.0625f * R.wf[2];
+        const float wxl = R.wlo[0], wy4l = 0.25f * R.wlo[1], wz16l = 0.0625f * R.wlo[2];
         float fx = 0.f, fy = 0.f, fz = 0.f, u = 0.f, w = 0.f;
         for (int m0 = 0; m0 < mm; m0 += NB) {
             uint32_t e[NB];
@@ -271,9 +277,11 @@ __global__ void __launch_bounds__(TILE) k_half_pairs(Arrays A, Scal S, int cur)
             for (int k = 0; k < NB; ++k) pj[k] = (m0 + k < mm) ? __ldg(pos + (e[k] >> IDX_SHIFT)) : pi;
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                const float dx = fmaf(offx_raw(e[k]) - 8388609.0f, wx, pj[k].x - pi.x);
-                const float dy = fmaf(offy_raw(e[k]) - 8388612.0f, wy4, pj[k].y - pi.y);
-                const float dz = fmaf(offz_raw(e[k]) - 8388624.0f, wz16, pj[k].z - pi.z);
+                const float ox = offx_raw(e[k]) - 8388609.0f, oy = offy_raw(e[k]) - 8388612.0f;
+                const float oz = offz_raw(e[k]) - 8388624.0f;
+                const float dx = fmaf(ox, wxl, fmaf(ox, wx, pj[k].x - pi.x));
+                const float dy = fmaf(oy, wy4l, fmaf(oy, wy4, pj[k].y - pi.y));
+                const float dz = fmaf(oz, wz16l, fmaf(oz, wz16, pj[k].z - pi.z));
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (m0 + k < mm && r2 < S.rc2f) {
                     const float ri2 = rcp_nr(r2);
@@ -359,7 +367,7 @@ __device__ __forceinline__ void chain_terms(const Arrays& A, const Scal& S, cons
                 int dc = cj[x] - ci[x];
                 if (2 * dc > R.nc[x]) dc -= R.nc[x];
                 if (2 * dc < -R.nc[x]) dc += R.nc[x];
-                r[d][x] = (pp[x] - pc[x]) + float(dc) * R.wf[x];
+                r[d][x] = fmaf(float(dc), R.wlo[x], (pp[x] - pc[x]) + float(dc) * R.wf[x]);
             }
         }
     }
@@ -466,13 +474,12 @@ __global__ void __launch_bounds__(TILE) k_chain_terms(Arrays A, Scal S, int cur)
 
 // Leapfrog kick and drift of one atom (Sec. 4.3 item 1) from its force a: MD_MIXED advances the
 // FP64 state (v, x), MD_FP32 the FP32 velocity v32 and position pi; pn receives the FP32
-// cell-local position of step n+1.  FP32<->FP64 conversions run on the integer pipe (bit for bit
-// the hardware ones).  Returns |x_{n+1} - x_n|^2 measured on the FP32 positions (the
-// refresh metric unless the rule is DISP).  With PROPS, part receives this atom's terms of the
-// props at step n in FP32 -- u_i, |v_n|^2, the virial and v_n -- which the warp sums in FP32 and
-// everything beyond the warp sums in FP64 (the MD_MIXED contract): v_n = v + c f from the FP32
-// rounding of the stored velocity, so the props cost no FP64 arithmetic (1/64 of the FP32 rate
-// on GB300).
+// cell-local position of step n+1.  FP32<->FP64 conversions round to nearest.  Returns
+// |x_{n+1} - x_n|^2 measured on the FP32 positions (the refresh metric unless the rule is DISP).
+// With PROPS, part receives this atom's terms of the props at step n in FP32 -- u_i, |v_n|^2,
+// the virial and v_n -- which the warp sums in FP32 and beyond the warp exactly (fixed point; the
+// MD_MIXED contract allows FP64 there): v_n = v + c f from the FP32 rounding of the stored
+// velocity, so the props cost no FP64 arithmetic (1/64 of the FP32 rate on GB300).
 template <int MODE, bool PROPS>
 __device__ __forceinline__ float kick_drift(const Scal& S, int vhalf, const float4& pi, const AccF& a,
                                             double (&v)[3], double (&x)[3], float (&v32)[3], float (&pn)[3],

@@ -54,6 +54,7 @@ struct NaView {
 struct NaGeom {
     double L[3], w[3], s[3];
     float wf[3];
+    float wlo[3];          // (float) (w - wf), added after o wf to keep the distances unbiased
     int nc[3];
     int ncells;
     int n;
@@ -177,9 +178,9 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_forces(NaView V, NaGeom G, do
                     const int j = V.perm[k];
                     if (j == i) continue;
                     const float4 pj = V.pos[j];
-                    const float dx = fmaf(float(ox), G.wf[0], pj.x - pi.x);
-                    const float dy = fmaf(float(oy), G.wf[1], pj.y - pi.y);
-                    const float dz = fmaf(float(oz), G.wf[2], pj.z - pi.z);
+                    const float dx = fmaf(float(ox), G.wlo[0], fmaf(float(ox), G.wf[0], pj.x - pi.x));
+                    const float dy = fmaf(float(oy), G.wlo[1], fmaf(float(oy), G.wf[1], pj.y - pi.y));
+                    const float dz = fmaf(float(oz), G.wlo[2], fmaf(float(oz), G.wf[2], pj.z - pi.z));
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     if (r2 < G.rc2f) {
                         const float ri2 = __frcp_rn(r2);
@@ -230,6 +231,7 @@ int md_forces_static(const md_params* p, int64_t n, const double* x, double* f, 
         G.w[a] = L / q;
         G.s[a] = q / L;
         G.wf[a] = float(G.w[a]);
+        G.wlo[a] = float(G.w[a] - double(G.wf[a]));
         if (int64_t(G.ncells) * G.nc[a] > NA_MAX_CELLS)
             return na_fail(MD_ERR_INVALID_ARG, "md_forces_static handles at most " + std::to_string(NA_MAX_CELLS) +
                                                    " cells of side >= rc");

@@ -501,6 +501,33 @@ def test_full_size_sampled(name):
         assert np.abs((ser[:, 1] + ser[:, 2]) - (po[:k, 0] + po[:k, 1])).max() / n <= 1e-6
 
 
+def test_props_rows_of_dense_replicas_match_oracle():
+    # uneven replicas up to rho = 0.9, perturbed: U/N up to 3.3, where a biased FP32 reciprocal
+    # in the pair terms put E/N 2.4e-6 off; the fixed-point props of every step against the
+    # oracle's, replica by replica
+    specs = inputs.replica_specs(6, 300, 3000, 0.6, 0.9, seed=31)
+    states = [(inputs.perturb(xr, br, 0.08, 90 + r), vr, br)
+              for r, (xr, vr, br) in enumerate(inputs.replica_states(specs, 1.0, seed=31))]
+    n_rep = [sp[0] for sp in specs]
+    x = np.concatenate([st[0] for st in states])
+    v = np.concatenate([st[1] for st in states])
+    s = MDSystem(x, v, n_rep=n_rep, boxes=np.stack([st[2] for st in states]), rc=WCA_RC, skin=0.4,
+                 precision="mixed", props_every=1)
+    s.integrate(50)
+    xg, vg, _ = s.state()
+    ser = s.series(64)
+    s.close()
+    off = 0
+    for r, (xr, vr, br) in enumerate(states):
+        n = xr.shape[0]
+        xo, vo, po, _ = oracle.run(xr, vr, br, oracle.pot(), dt=0.005, nsteps=50)
+        assert np.abs(min_image(xg[off:off + n] - xo, br)).max() <= 1e-4
+        assert rel_l2(vg[off:off + n], vo) <= 1e-4
+        assert np.array_equal(ser[r, :, 0], np.arange(50))
+        assert np.abs((ser[r, :, 1] + ser[r, :, 2]) - (po[:50, 0] + po[:50, 1])).max() / n <= 1e-6
+        off += n
+
+
 # ---------------------------------------------------------------------------------------------
 # the list-free step kernel (step kernel 4: no neighbour matrix, the 27 cells every step)
 # ---------------------------------------------------------------------------------------------
