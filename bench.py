@@ -305,7 +305,9 @@ def run_gb300(args, rank, world, local_rank):
     if args.tune:
         from paper_2003_14061_gb300 import tune as gtune
         s.integrate(max(args.warmup // 2, 16))     # melt first: tune on the fluid
-        tuned = gtune.tune(s, steps=args.tune_steps)
+        # the neighbour-matrix kernel (the paper's method, deterministic); the list-free and
+        # half-list kernels are forms of their own
+        tuned = gtune.tune(s, steps=args.tune_steps, step_kernels=(1,))
     if args.no_graph:          # direct launches (ncu cannot profile kernels of graphs with IF nodes)
         s.set_tuning(use_graph=2)
     stream = s.stream
@@ -481,7 +483,7 @@ def measure_form(label, x, v, geo, dev, precision, rc, skin, steps, warmup, tune
     if fixed:
         s.set_tuning(**fixed)
     elif tune:
-        gtune.tune(s, steps=64)
+        gtune.tune(s, steps=64, step_kernels=(1,))    # the neighbour-matrix kernel; 4 and 5 have forms of their own
     s.integrate(max(warmup // 2, 16))
     p0 = s.props()
     ms = _event_ms(s, lambda: s.integrate(steps))

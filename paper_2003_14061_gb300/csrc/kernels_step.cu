@@ -710,6 +710,36 @@ __device__ __forceinline__ void props_warp_flush(const Arrays& A, int r, PropsAc
     pa.vm = 0.0f;
 }
 
+// The same with the warp's sums in shared memory (acc[q] for quantity q, vm the maximum; each
+// entry touched by one lane only), which keeps them out of the registers of the per-SM step
+// kernel, whose pair loop runs at the register bound.
+__device__ __forceinline__ void props_warp_add_sh(const Arrays& A, int r, float (&p)[NPROP], long long* acc, float* vm)
+{
+    int q;
+    float m;
+    const float a1 = warp_partials(p, q, m);
+    if ((threadIdx.x & 3) == 0 && q != NPROP - 1) {
+        if (fabsf(a1) < PROPS_FIX_MAX) acc[q] += __float2ll_rn(a1 * PROPS_FIX);
+        else atomicAdd(&A.rs[r].pbig[q], double(a1));
+    }
+    if ((threadIdx.x & 31) == 0) *vm = fmaxf(*vm, m);
+}
+
+__device__ __forceinline__ void props_warp_flush_sh(const Arrays& A, int r, long long* acc, float* vm)
+{
+    const int lane = threadIdx.x & 31;
+    if ((lane & 3) == 0 && (lane >> 2) < NPROP - 1) {
+        const long long a = acc[lane >> 2];
+        if (a != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&A.rs[r].pacc[lane >> 2]), static_cast<unsigned long long>(a));
+        acc[lane >> 2] = 0;
+    }
+    if (lane == 0) {
+        atomicMax(&A.rs[r].pvmax2, __float_as_uint(*vm));
+        *vm = 0.0f;
+    }
+    __threadfence();
+}
+
 // one warp-tile's props: FP64 lanes (MD_FP64) store the warp's partials for k_props_reduce, FP32
 // lanes add them to the warp's fixed-point sums
 __device__ __forceinline__ void props_take(const Arrays&, int, double (&p)[NPROP], PropsAcc&, double* dst)
@@ -1051,10 +1081,10 @@ __device__ __forceinline__ int ld_relaxed_gpu(const int* p)
 // warp-tiles runs the refresh bookkeeping.
 __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& S, int r, float run_max, int wtiles,
                                                    cudaGraphConditionalHandle cond, int use_cond,
-                                                   PropsAcc* pa = nullptr)
+                                                   long long* pacc = nullptr, float* pvm = nullptr)
 {
-    if (pa) {
-        props_warp_flush(A, r, *pa);
+    if (pacc) {
+        props_warp_flush_sh(A, r, pacc, pvm);
         __syncwarp();
     }
     const float m = warp_max(run_max);
@@ -1064,7 +1094,7 @@ __device__ __forceinline__ void flush_replica_warp(const Arrays& A, const Scal& 
         const int done = atomicAdd(&A.rs[r].tiles_done, wtiles) + wtiles;
         if (done == A.rep[r].ntiles * (TILE / 32)) {
             __threadfence();
-            finish_replica_step(A, S, r, cond, use_cond, pa ? 1 : 0);
+            finish_replica_step(A, S, r, cond, use_cond, pacc ? 1 : 0);
         }
     }
     __syncwarp();
@@ -1130,8 +1160,15 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
     int c0 = (w0 >= 0 && SRC == 0) ? __ldcs(A.nbr_count + int64_t(w0) * 32 + lane) : 0;   // w0's counts
     int run_r = -1, run_cnt = 0;
     float run_max = 0.0f;
-    PropsAcc pa{0, 0.0f};
-    PropsAcc* const pfix = PROPS ? &pa : nullptr;
+    __shared__ long long s_pacc[TILE / 32][8];
+    __shared__ float s_pvm[TILE / 32];
+    long long* const pacc = PROPS ? s_pacc[threadIdx.x >> 5] : nullptr;
+    float* const pvm = PROPS ? &s_pvm[threadIdx.x >> 5] : nullptr;
+    if (PROPS) {
+        if (lane < 8) pacc[lane] = 0;
+        if (lane == 0) *pvm = 0.0f;
+        __syncwarp();
+    }
     while (w0 >= 0) {
         int pend = 0;
         const bool pending = home_open && w1 >= 0;
@@ -1161,7 +1198,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         const int t = w0 / (TILE / 32);
         const int r = A.tile_rep[t];
         if (r != run_r) {
-            if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond, pfix);
+            if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond, pacc, pvm);
             run_r = r;
             run_cnt = 0;
             run_max = 0.0f;
@@ -1219,7 +1256,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         }
         run_max = fmaxf(run_max, metric);
         run_cnt += 1;
-        if (PROPS) props_warp_add(A, r, part, pa);
+        if (PROPS) props_warp_add_sh(A, r, part, pacc, pvm);
         int w2 = -1;
         if (w1 >= 0) {
             // the rows of W below the next warp-tile's largest count into L2
@@ -1237,7 +1274,7 @@ __global__ void __launch_bounds__(TILE, MINB) k_step_sm(Arrays A, Scal S, int cu
         w1 = w2;
         c0 = c1;                                 // read one warp-tile ahead
     }
-    if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond, pfix);
+    if (run_r >= 0) flush_replica_warp(A, S, run_r, run_max, run_cnt, cond, use_cond, pacc, pvm);
     // the last warp of the launch resets the counters; the next launch is ordered after this one
     if (lane == 0) {
         __threadfence();
