@@ -235,9 +235,11 @@ int md_cells_per_axis(const md_system* s, int32_t r, int32_t* nc);
  * size mattered little on its GPU and warned that this need not hold in general (Sec. 4.1
  * item 2).  A field left 0 keeps its current value. */
 typedef struct {
-    int32_t ctas_per_sm;     /* persistent CTAs per SM for the tile loops (1..64); grid = SMs x this;
-                                the step kernel is also compiled to fit 4, 8, 12 or 16 CTAs per SM
-                                (the largest not above this) and its grid is capped at residency */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM of the step kernel and the other per-step
+                                tile loops (1..64); the step kernel is also compiled to fit 4, 8,
+                                12 or 16 CTAs per SM (the largest not above this) and its grid is
+                                capped at residency.  The rebuild kernels (binning, scatter,
+                                reorder, neighbour build) always run at their full residency */
     int32_t nbr_batch;       /* W entries each thread loads together in the pair loop: 2, 4 or 8 */
     int32_t build_batch;     /* neighbour build: 2 or 4 = one thread per atom loading that many
                                 candidates together; 32 = one warp per cell, each row of
