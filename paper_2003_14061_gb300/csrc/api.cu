@@ -186,7 +186,7 @@ size_t carve(const Plan& P, char* base, Arrays* A)
     a.W = c.take<uint32_t>(ns * size_t(P.cap));
     if (P.rule == MD_REBUILD_DISP) a.xref = c.take<float4>(ns);
     a.perm = c.take<int32_t>(ns);
-    if (!f64) a.psort = c.take<float4>(ns);
+    if (!f64) a.psort = c.take<float4>(ns + PSORT_PAD);       // readable past the last atom
     if (!f64) a.tile_win = c.take<int2>(size_t(P.ntiles) * 9);
     if (!f64) {
         a.fbuf = c.take<float4>(ns);

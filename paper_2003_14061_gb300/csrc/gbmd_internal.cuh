@@ -36,6 +36,9 @@ constexpr int SCAN_CHUNK = 2048;          // cells per block of the prefix sum
 constexpr int PROPS_SPLIT_MAX = 2048;     // CTAs per replica in the first level of the final sums
 constexpr int ADJ_VPART = 128;            // blocks of the |v_S|^2 partial sums
 
+// entries of psort past the last atom, so that a build batch may read past a row's end
+constexpr int PSORT_PAD = 8;
+
 enum ErrBits { ERR_NBR_OVERFLOW = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
 struct Rep {                  // per replica, fixed after creation

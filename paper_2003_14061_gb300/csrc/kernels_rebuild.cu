@@ -669,6 +669,35 @@ __device__ __forceinline__ void nbr_test(const float4& p, const float2& npxy, fl
 constexpr int BUILD_CHUNK = 4;
 #define build_tile(q) ((((q) / BUILD_CHUNK) * int(gridDim.x) + int(blockIdx.x)) * BUILD_CHUNK + (q) % BUILD_CHUNK)
 
+// Two candidates of a row in one pass of packed FP32x2 operations (candidate a in lane x, b in
+// lane y); each lane rounds as nbr_test does, and a is appended before b, so W is the same entry
+// for entry.
+__device__ __forceinline__ void nbr_test2(const float4& pa, const float4& pb, float2 nx, float2 ny, float2 nz,
+                                          float2 offx, float offy, float offz, bool va, bool vb, uint32_t ca,
+                                          uint32_t cb, int me, float rl2, uint32_t*& wp, int& m, int cap,
+                                          int64_t stride, int half)
+{
+    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(pa.x, pb.x), nx), offx);
+    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(pa.y, pb.y), ny), make_float2(offy, offy));
+    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(pa.z, pb.z), nz), make_float2(offz, offz));
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const int ja = __float_as_int(pa.w), jb = __float_as_int(pb.w);
+    if (va && r2.x < rl2 && (half ? ja > me : ja != me)) {
+        if (m < cap) {
+            *wp = (uint32_t(ja) << IDX_SHIFT) | ca;
+            wp += stride;
+        }
+        ++m;
+    }
+    if (vb && r2.y < rl2 && (half ? jb > me : jb != me)) {
+        if (m < cap) {
+            *wp = (uint32_t(jb) << IDX_SHIFT) | cb;
+            wp += stride;
+        }
+        ++m;
+    }
+}
+
 // STAGE: a thread appends its column of W to shared memory (stride TILE) instead of W itself,
 // and each warp then writes its columns row by row: 32 consecutive slots of a row are 128
 // contiguous bytes, where entries written as found land one at a time in partly written sectors.
@@ -683,6 +712,7 @@ __device__ __forceinline__ void flush_columns(const Arrays& A, const Scal& S, co
 template <int BB, bool STAGE>
 __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur)
 {
+    static_assert(BB % 2 == 0, "candidates are tested in pairs");
     extern __shared__ uint32_t sW[];                 // STAGE: [cap][TILE] columns of this tile
     if (!A.g->any_rebuild) return;
     const int64_t wstride = STAGE ? int64_t(TILE) : S.nslots;
@@ -723,6 +753,7 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
             const float dhi2[3] = {(w0 - pi.x) * (w0 - pi.x), (w1 - pi.y) * (w1 - pi.y), (w2 - pi.z) * (w2 - pi.z)};
             const float2 npxy = make_float2(-pi.x, -pi.y);
             const float npz = -pi.z;
+            const float2 nx2 = make_float2(-pi.x, -pi.x), ny2 = make_float2(-pi.y, -pi.y), nz2 = make_float2(-pi.z, -pi.z);
             for (int oz = -1; oz <= 1; ++oz) {
                 int nz = cz + oz; nz += (nz < 0) ? R.nc[2] : 0; nz -= (nz >= R.nc[2]) ? R.nc[2] : 0;
                 const float offz = float(oz) * w2;
@@ -740,17 +771,21 @@ __global__ void __launch_bounds__(TILE) k_build_sorted(Arrays A, Scal S, int cur
                         const int b0 = cs[row + cx - 1], b1 = cs[row + cx], b2 = cs[row + cx + 1];
                         const int kb = use_l ? b0 : b1;
                         const int ke = use_r ? cs[row + cx + 2] : b2;
+                        // psort has PSORT_PAD entries past its end, so the last batch reads
+                        // past ke unclamped (those lanes are invalid)
                         for (int k0 = kb; k0 < ke; k0 += BB) {
                             float4 pj[BB];
 #pragma unroll
-                            for (int u = 0; u < BB; ++u) pj[u] = ps[min(k0 + u, ke - 1)];
+                            for (int u = 0; u < BB; ++u) pj[u] = ps[k0 + u];
 #pragma unroll
-                            for (int u = 0; u < BB; ++u) {
-                                const int k = k0 + u;
-                                const uint32_t c = uint32_t(k >= b1) + uint32_t(k >= b2);   // o_x + 1
-                                const float offx = (k < b1) ? -w0 : ((k < b2) ? 0.0f : w0);
-                                nbr_test(pj[u], npxy, npz, offx, offy, offz, k < ke, codeyz | c, me, rl2, wp, m,
-                                         S.cap, wstride, S.half_list);
+                            for (int u = 0; u < BB; u += 2) {
+                                const int ka = k0 + u, kb2 = ka + 1;
+                                const uint32_t ca = uint32_t(ka >= b1) + uint32_t(ka >= b2);   // o_x + 1
+                                const uint32_t cb = uint32_t(kb2 >= b1) + uint32_t(kb2 >= b2);
+                                const float2 offx = make_float2((ka < b1) ? -w0 : ((ka < b2) ? 0.0f : w0),
+                                                                (kb2 < b1) ? -w0 : ((kb2 < b2) ? 0.0f : w0));
+                                nbr_test2(pj[u], pj[u + 1], nx2, ny2, nz2, offx, offy, offz, ka < ke, kb2 < ke,
+                                          codeyz | ca, codeyz | cb, me, rl2, wp, m, S.cap, wstride, S.half_list);
                             }
                         }
                     } else {
