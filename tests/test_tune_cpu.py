@@ -86,3 +86,46 @@ def test_cache_round_trip(fake_timing, tmp_path):
     assert again["best"] == first["best"]
     assert s.steps == 0                            # served from the cache: nothing timed
     assert s.set_calls == [first["best"]]
+
+
+class PhaseSystem(FakeSystem):
+    """Per-phase timings and rebuild counters as the library reports them: a step phase of a
+    fixed cost per step and rebuilds of a fixed cost whose number per trial varies."""
+
+    def __init__(self, rebuilds_per_trial):
+        super().__init__()
+        self.plan = list(rebuilds_per_trial)
+        self.rebuilds = 0
+        self.timing_on = False
+        self.ph = None
+
+    def props(self):
+        return [{"rebuilds": self.rebuilds}]
+
+    def set_timing(self, on=True):
+        self.timing_on = on
+
+    def integrate(self, n):
+        super().integrate(n)
+        if self.timing_on:
+            k = self.plan.pop(0)
+            self.rebuilds += k
+            self.ph = {"step": (0.2 * n, n, n), "bin": (0.1 * k, n, n), "reorder": (0.0, 0, 0),
+                       "build": (0.9 * k, n, n), "props": (0.0, 0, 0), "other": (0.0, 0, 0)}
+
+    def timing(self):
+        return self.ph
+
+
+def test_score_does_not_depend_on_the_rebuilds_that_fell_in_a_trial():
+    # the same shape timed twice, with 9 and then 14 rebuilds falling into the 100 timed steps:
+    # the score is step time + time per rebuild x the rebuild rate over the search, so the
+    # second trial scores the same shape no worse than the first
+    s = PhaseSystem([9, 14])
+    rate = tune._Rate()
+    a = tune._time_steps(s, 100, rate)
+    b = tune._time_steps(s, 100, rate)
+    assert a == pytest.approx(0.2 + 1.0 * 9 / 100)
+    assert b == pytest.approx(0.2 + 1.0 * 23 / 200)
+    # whole-step timing would have scored the second trial 0.05 ms worse
+    assert abs(b - a) < 0.05
