@@ -106,7 +106,10 @@ __device__ __forceinline__ AccF pair_loop_f32(const Scal& S, const Rep& R, float
     for (int m0 = 0; m0 < mm; m0 += NB) {
         float4 pj[NB];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) pj[k] = (m0 + k < mm) ? pr(e[k]) : pi;
+        // entries past mm are 0 (slot 0, a valid address) and masked below; with 4 or 8 entries
+        // per batch the unconditional gathers measured faster (LJ, 8 per batch: 2.61 against
+        // 2.73 ms), with 2 slower (0.227 against 0.206 ms), so the select stays there
+        for (int k = 0; k < NB; ++k) pj[k] = (NB >= 4 || m0 + k < mm) ? pr(e[k]) : pi;
         uint32_t en[NB];
 #pragma unroll
         for (int k = 0; k < NB; ++k) en[k] = (m0 + NB + k < mm) ? wr(m0 + NB + k) : 0u;
