@@ -501,6 +501,29 @@ def test_full_size_sampled(name):
         assert np.abs((ser[:, 1] + ser[:, 2]) - (po[:k, 0] + po[:k, 1])).max() / n <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_props_of_overlapping_atoms_take_the_fp64_path(prec):
+    # two atoms 0.15 sigma apart: each has u_i of about 3e10, so its warp's sum is beyond the
+    # fixed-point range (2^31) and goes to the FP64 overflow sums; the step-0 row must still be
+    # the oracle's to FP32 accuracy (dt is tiny so that the pair does not fly apart).  The bar:
+    # the FP32 cell-local positions carry up to 1.2e-7 of rounding in a 0.15 distance, 8e-7
+    # relative, which u ~ r^-12 and the virial ~ r^-12 raise twelvefold: 2e-5 relative; a
+    # dropped or wrapped sum would be off by the whole value
+    x, box = inputs.fcc_lattice(4, 0.8)
+    x = x.copy()
+    x[1] = x[0] + np.array([0.15, 0.0, 0.0])
+    v = inputs.maxwell(x.shape[0], 1.0, seed=3)
+    s = MDSystem(x, v, box, rc=WCA_RC, skin=0.4, precision=prec, dt=1e-12, props_every=1)
+    s.integrate(1)
+    row = s.series(4)[0][0]
+    s.close()
+    op = oracle.props(x, v, box, oracle.pot())
+    assert op[0] > 1e10
+    assert abs(row[1] - op[0]) <= 2e-5 * op[0]                 # U
+    assert abs(row[2] - op[1]) <= 1e-6 * abs(op[1]) + 1e-6     # K
+    assert abs(row[3] - op[2]) <= 2e-5 * abs(op[2])            # virial
+
+
 def test_props_rows_of_dense_replicas_match_oracle():
     # uneven replicas up to rho = 0.9, perturbed: U/N up to 3.3, where a biased FP32 reciprocal
     # in the pair terms put E/N 2.4e-6 off; the fixed-point props of every step against the
