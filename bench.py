@@ -297,7 +297,7 @@ def run_gb300(args, rank, world, local_rank):
     w = WORKLOADS[args.workload]
     x, v, geo = make_inputs(args.workload, rank, args.ncell)
     n = x.shape[0]
-    s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
+    s = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision=args.precision, reorder_every=100,
                  rebuild_rule=RULE, props_every=args.props_every, **geo)
     if args.ctas_per_sm or args.nbr_batch or args.build_batch:
         s.set_tuning(ctas_per_sm=args.ctas_per_sm, nbr_batch=args.nbr_batch, build_batch=args.build_batch)
@@ -354,9 +354,11 @@ def run_gb300(args, rank, world, local_rank):
     s.set_tuning(use_graph=2 if args.no_graph else 1)
     step_ms, step_calls, step_launches = phases["step"]
     # with the props in every step, every timed launch is the step kernel's props form
-    roof_kernel = "k_step_sm<MD_MIXED, props>" if args.props_every == 1 else "k_step_sm<MD_MIXED>"
+    mode = {"mixed": "MD_MIXED", "fp32": "MD_FP32", "fp64": "MD_FP64"}[args.precision]
+    roof_kernel = (f"k_step_sm<{mode}, props>" if args.props_every == 1 else f"k_step_sm<{mode}>") \
+        if args.precision != "fp64" else "k_step<MD_FP64>"
     peak, peak_kind = load_peaks()
-    bpa = algorithmic_bytes_per_atom_step(mean_nbrs, "mixed", RULE)
+    bpa = algorithmic_bytes_per_atom_step(mean_nbrs, args.precision, RULE)
     per_launch_ms = step_ms / max(step_calls, 1)
     achieved = bpa * n / (per_launch_ms * 1e-3) / 1e9
 
@@ -364,7 +366,7 @@ def run_gb300(args, rank, world, local_rank):
     # energy reduction F2 fused) and a device-to-host read of that step's props row into pinned
     # memory; the state goes host-to-device at the start and device-to-host at the end
     e2e_steps = min(args.steps, args.e2e_steps)
-    se = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision="mixed", reorder_every=100,
+    se = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision=args.precision, reorder_every=100,
                   rebuild_rule=RULE, props_every=1, **geo)
     se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "build_stage", "step_kernel")})
     se.integrate(32)                                     # capture its graphs outside the timing:
@@ -419,9 +421,11 @@ def run_gb300(args, rank, world, local_rank):
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
             "config": {"workload": w["desc"] if not args.ncell else f"{w['desc']} (resized: fcc {args.ncell}^3)",
-                       "atoms_per_gpu": n, "precision": "FP32 pair forces, FP64 state",
+                       "atoms_per_gpu": n, "precision": {"mixed": "FP32 pair forces, FP64 state",
+                                                        "fp32": "FP32 pair forces and state",
+                                                        "fp64": "FP64 throughout"}[args.precision],
                        "skin": w["skin"], "rc": w["rc"], "dt": DT, "reorder_every": 100,
                        "rebuild_rule": "accumulated bound dt*max|v| on the largest displacement since the last rebuild > skin/2 (the paper's criterion; the exact-displacement rule is the form wca4m_mixed_disp)",
                        "l2": "inputs larger than L2 (state %.2f GB)" % (s.workspace_bytes / 1e9),
@@ -687,6 +691,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=300)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="wca4m", choices=list(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
+                    help="precision of the timed system (the default is the benchmark's)")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--ncell", type=int, default=0, help="fcc cells per axis (smaller case for profiling)")
     ap.add_argument("--nbr-batch", type=int, default=0)
