@@ -368,7 +368,8 @@ def run_gb300(args, rank, world, local_rank):
     e2e_steps = min(args.steps, args.e2e_steps)
     se = MDSystem(x, v, device=dev, rc=w["rc"], skin=w["skin"], dt=DT, precision=args.precision, reorder_every=100,
                   rebuild_rule=RULE, props_every=1, **geo)
-    se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "build_stage", "step_kernel")})
+    se.set_tuning(**{k: s.tuning()[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "build_stage", "step_kernel",
+                                                     "reorder_every")})
     se.integrate(32)                                     # capture its graphs outside the timing:
     se.integrate(1)                                      # the 16-step ones and the one-step ones
     se.integrate(1)                                      # from either position buffer

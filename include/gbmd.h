@@ -278,6 +278,10 @@ typedef struct {
                                 column of W in shared memory and the warps write whole rows (128
                                 contiguous bytes per row for 32 atoms; for matrices far larger
                                 than L2), 2 = each entry written to W as found */
+    int32_t reorder_every;   /* the reorder of atoms by cell (Sec. 4.1 item 1): at the first rebuild
+                                at least this many steps after the last reorder, or -1 = at
+                                every rebuild; starts as md_params.reorder_every (0 there reads
+                                as -1 here); 0 keeps the current value in md_set_tuning */
 } md_tuning;
 int md_set_tuning(md_system* s, const md_tuning* t);
 int md_get_tuning(const md_system* s, md_tuning* t);

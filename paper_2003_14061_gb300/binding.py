@@ -66,7 +66,8 @@ class md_props(ctypes.Structure):
 class md_tuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("nbr_batch", ctypes.c_int32),
                 ("build_batch", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("step_kernel", ctypes.c_int32), ("build_stage", ctypes.c_int32)]
+                ("step_kernel", ctypes.c_int32), ("build_stage", ctypes.c_int32),
+                ("reorder_every", ctypes.c_int32)]
 
 
 class md_chains(ctypes.Structure):

@@ -443,7 +443,8 @@ int apply_tuning(md_system* s)
     s->L.build_stage = s->tune.build_stage == 1 ? 1 : 0;
     s->L.step_kernel = (s->S.mode == MD_FP64) ? 1 : s->tune.step_kernel;
     // the list-free kernel reads each row of cells as a run of slots: atoms reorder at every rebuild
-    s->S.reorder_every = (s->L.step_kernel == 4) ? 0 : s->p.reorder_every;
+    // tune.reorder_every: -1 = at every rebuild, else every that many steps
+    s->S.reorder_every = (s->L.step_kernel == 4 || s->tune.reorder_every < 0) ? 0 : s->tune.reorder_every;
     s->S.half_list = (s->L.step_kernel == 5) ? 1 : 0;      // W keeps each pair once
     bulk_shape(s->S, per_sm, s->smem_per_sm, s->smem_per_cta, &s->L.bulk_rows, &s->L.bulk_smem);
     stage_shape(per_sm, s->smem_per_sm, &s->L.stage_cap, &s->L.stage_smem);
@@ -690,6 +691,7 @@ int md_create_batch(const md_params* p, int32_t nrep, const int64_t* n_rep, cons
     s->tune.build_batch = 2;
     s->tune.use_graph = 1;
     s->tune.step_kernel = 1;
+    s->tune.reorder_every = s->p.reorder_every == 0 ? -1 : s->p.reorder_every;
     s->tune.build_stage = 2;            // 2 = off (0 keeps the current value in md_set_tuning)
     apply_tuning(s);
 
@@ -729,7 +731,7 @@ int md_destroy(md_system* s)
 int md_bin_cells(md_system* s)
 {
     if (!s) return fail(MD_ERR_INVALID_ARG, "system is NULL");
-    GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, s->p.reorder_every == 0 ? 1 : 0));
+    GBMD_CUDA(launch_force_rebuild(s->A, s->S, s->L, s->S.reorder_every == 0 ? 1 : 0));
     GBMD_CUDA(launch_bin_only(s->A, s->S, s->L, s->cur, false));
     s->binned_fresh = true;
     return MD_OK;
@@ -1123,6 +1125,7 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->use_graph < 0 || t->use_graph > 2) return fail(MD_ERR_INVALID_ARG, "use_graph must be 0, 1 or 2");
     if (t->step_kernel < 0 || t->step_kernel > 5) return fail(MD_ERR_INVALID_ARG, "step_kernel must be 0..5");
     if (t->build_stage < 0 || t->build_stage > 2) return fail(MD_ERR_INVALID_ARG, "build_stage must be 0, 1 or 2");
+    if (t->reorder_every < -1) return fail(MD_ERR_INVALID_ARG, "reorder_every must be >= -1");
     const int old_kernel = s->L.step_kernel;
     if (t->ctas_per_sm) s->tune.ctas_per_sm = t->ctas_per_sm;
     if (t->nbr_batch) s->tune.nbr_batch = t->nbr_batch;
@@ -1130,6 +1133,7 @@ int md_set_tuning(md_system* s, const md_tuning* t)
     if (t->use_graph) s->tune.use_graph = t->use_graph;
     if (t->step_kernel) s->tune.step_kernel = t->step_kernel;
     if (t->build_stage) s->tune.build_stage = t->build_stage;
+    if (t->reorder_every) s->tune.reorder_every = t->reorder_every;
     s->drop_graphs();          // launch shapes are baked into captured graphs
     int rc = apply_tuning(s);
     if (rc) return rc;

@@ -241,14 +241,15 @@ class MDSystem:
         return vacf, msd, cnt
 
     def set_tuning(self, ctas_per_sm: int = 0, nbr_batch: int = 0, build_batch: int = 0, use_graph: int = 0,
-                   step_kernel: int = 0, build_stage: int = 0):
+                   step_kernel: int = 0, build_stage: int = 0, reorder_every: int = 0):
         """Launch shapes (0 keeps the current value); use_graph: 1 = CUDA graphs, 2 = direct;
         step_kernel: 1 = per-thread loads with L2 prefetch, 2 = bulk-copy shared-memory ring,
         3 = staged cell-row windows in shared memory, 4 = list-free (27 cells every step),
         5 = half neighbour list with atomic reactions; build_stage: 1 = the build writes W rows
-        from shared memory, 2 = entry by entry."""
+        from shared memory, 2 = entry by entry; reorder_every: reorder by cell every that many
+        steps (at a rebuild), -1 = at every rebuild."""
         t = B.md_tuning(int(ctas_per_sm), int(nbr_batch), int(build_batch), int(use_graph), int(step_kernel),
-                        int(build_stage))
+                        int(build_stage), int(reorder_every))
         self._call("md_set_tuning", ctypes.byref(t))
 
     def set_timing(self, enable: bool = True):

@@ -13,7 +13,8 @@ Search: coordinate descent over (step kernel, ctas_per_sm, nbr_batch) for the st
 per-thread kernel at register-bound residencies, the list-free and half-list kernels, and on
 request the shared-memory ring and the staged-neighbour kernel (2 and 3, slower on every measured
 workload) at the residencies their shared memory allows -- then build_batch and build_stage for
-the neighbour build.
+the neighbour build, then the reorder policy (every 100 steps or at every rebuild: the paper's
+reorder, Sec. 4.1 item 1, is a trade between the reorder's cost and the locality it restores).
 
 Measurement: each candidate runs with direct launches and the library's per-phase CUDA events,
 and is scored as (step-phase ms per step) + (rebuild-phase ms per rebuild) x (rebuilds per step
@@ -37,7 +38,8 @@ CTAS_RING = (2, 3, 4, 6)       # shared-memory ring step kernel (shared-memory-b
 CTAS_STAGED = (4, 6, 8)        # staged-neighbour step kernel (register- and shared-memory-bound)
 CTAS_CELLS = (4, 8, 12)        # list-free and half-list step kernels (register-bound residency)
 NBR_BATCH = (2, 4, 8)
-REBUILD_PHASES = ("bin", "reorder", "build")
+REBUILD_PHASES = ("bin", "build")
+REORDER = (100, -1)            # reorder every 100 steps, or at every rebuild
 BUILD_BATCH = (1, 2, 4, 32)
 BUILD_STAGE = (2, 1)           # the build writes W entry by entry, or rows from shared memory
 
@@ -49,32 +51,44 @@ def signature(system) -> str:
             f"rho{system.n / float((system.boxes.prod(axis=1)).sum()):.3f}")
 
 
-def _rebuilds(system) -> int:
-    return sum(int(p["rebuilds"]) for p in system.props())
+def _counts(system):
+    pr = system.props()
+    return sum(int(p["rebuilds"]) for p in pr), sum(int(p.get("reorders", 0)) for p in pr)
 
 
 class _Rate:
-    """Rebuilds per step over every trial so far (the same physical system throughout)."""
+    """Rebuilds per step over every trial so far (the same physical system throughout), and the
+    last measured cost of one reorder."""
     steps = 0
     rebuilds = 0
+    reorder_ms = None
 
 
 def _time_steps(system, steps: int, rate: _Rate = None) -> float:
     """Score of the current launch shape in ms per step (see the module docstring)."""
-    r0 = _rebuilds(system)
+    ro = system.tuning().get("reorder_every", 100)
+    r0, o0 = _counts(system)
     system.set_timing(True)
     system.integrate(steps)
     ph = system.timing()
     system.set_timing(False)
-    k = _rebuilds(system) - r0
+    r1, o1 = _counts(system)
+    k, kr = r1 - r0, o1 - o0
     step_ms = ph["step"][0] / steps
     rebuild_ms = sum(ph[name][0] for name in REBUILD_PHASES)
+    reorder_ms = ph["reorder"][0]
     if rate is None:
-        return step_ms + rebuild_ms / steps
+        return step_ms + (rebuild_ms + reorder_ms) / steps
     rate.steps += steps
     rate.rebuilds += k
     per_step = rate.rebuilds / rate.steps
-    return step_ms + (rebuild_ms / k * per_step if k else rebuild_ms / steps)
+    score = step_ms + (rebuild_ms / k * per_step if k else rebuild_ms / steps)
+    # reorders: every rebuild (ro = -1) or about every ro steps, at the cost of one measured reorder
+    if kr:
+        rate.reorder_ms = reorder_ms / kr
+    if rate.reorder_ms is not None:
+        score += rate.reorder_ms * (per_step if ro < 0 else 1.0 / max(ro, 1))
+    return score
 
 
 def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = False,
@@ -110,7 +124,8 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
         return ms
 
     cur = system.tuning()
-    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage")}
+    best = {k: cur[k] for k in ("ctas_per_sm", "nbr_batch", "build_batch", "step_kernel", "build_stage",
+                                "reorder_every")}
     best_ms = trial(**best)
     kernels = (1,) if system.params.precision == B.MD_FP64 else tuple(step_kernels)
     for sk in kernels:
@@ -125,6 +140,14 @@ def tune(system, steps: int = 128, cache: str | None = None, verbose: bool = Fal
     for bb in BUILD_BATCH:
         for stage in (BUILD_STAGE if bb != 32 else (best["build_stage"],)):
             cand = dict(best, build_batch=bb, build_stage=stage)
+            if json.dumps(cand, sort_keys=True) in trials:
+                continue
+            ms = trial(**cand)
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    if best["step_kernel"] != 4:          # the list-free kernel reorders at every rebuild anyway
+        for ro in REORDER:
+            cand = dict(best, reorder_every=ro)
             if json.dumps(cand, sort_keys=True) in trials:
                 continue
             ms = trial(**cand)

@@ -161,6 +161,30 @@ def test_trajectory_through_mid_run_reorders(prec, steps, reorder):
     assert abs(pr["E_per_atom"] - (po[-1, 0] + po[-1, 1]) / x.shape[0]) <= 1e-6
 
 
+def test_reorder_policy_is_a_tuning_choice():
+    # switched to a reorder at every rebuild and back mid-run: the reorders follow the policy and
+    # the trajectory stays the oracle's
+    s, x, v, box, rc, skin = make("wca2048", "mixed")
+    assert s.tuning()["reorder_every"] == 100
+    s.integrate(10)
+    p0 = s.props()[0]
+    s.set_tuning(reorder_every=-1)
+    s.integrate(60)
+    p1 = s.props()[0]
+    assert p1["rebuilds"] - p0["rebuilds"] >= 3
+    assert p1["reorders"] - p0["reorders"] == p1["rebuilds"] - p0["rebuilds"]
+    s.set_tuning(reorder_every=100)
+    s.integrate(30)
+    p2 = s.props()[0]
+    assert p2["reorders"] - p1["reorders"] <= 1
+    xg, vg, _ = s.state()
+    xo, vo, po, _ = oracle.run(x, v, box, oracle.pot(rc=rc), dt=0.005, nsteps=100, rule=1, skin=skin)
+    assert np.abs(min_image(xg - xo, box)).max() <= 1e-4
+    assert rel_l2(vg, vo) <= 1e-4
+    with pytest.raises(B.MDError):
+        s.set_tuning(reorder_every=-2)
+
+
 def test_repeat_runs_bit_identical():
     a, x, v, box, rc, skin = make("wca1372", "mixed")
     b, *_ = make("wca1372", "mixed")

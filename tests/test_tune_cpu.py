@@ -17,7 +17,7 @@ class FakeSystem:
     def __init__(self, precision=B.MD_MIXED):
         self.params = FakeParams(precision)
         self.t = {"ctas_per_sm": 8, "nbr_batch": 2, "build_batch": 2, "use_graph": 1, "step_kernel": 1,
-                  "build_stage": 2}
+                  "build_stage": 2, "reorder_every": 100}
         self.set_calls = []
         self.steps = 0
 
@@ -36,7 +36,7 @@ def cost(t):
     # a unique minimum at step kernel 1, 12 CTAs/SM, 4 entries per batch, build batch 4
     c = 1.0 + 0.1 * abs(t["ctas_per_sm"] - 12) + 0.05 * abs(t["nbr_batch"] - 4)
     c += {1: 0.0, 2: 0.5, 3: 0.7, 4: 0.9, 5: 0.6}[t["step_kernel"]] + {1: 0.1, 2: 0.02, 4: 0.0, 32: 0.3}[t["build_batch"]]
-    c += {1: 0.0, 2: 0.01}[t["build_stage"]]
+    c += {1: 0.0, 2: 0.01}[t["build_stage"]] + {100: 0.0, -1: 0.02}[t["reorder_every"]]
     return c
 
 
@@ -49,7 +49,9 @@ def fake_timing(monkeypatch):
 def test_search_finds_the_fastest_shape(fake_timing):
     s = FakeSystem()
     res = tune.tune(s, steps=64)
-    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1, "build_stage": 1}
+    assert res["best"] == {"ctas_per_sm": 12, "nbr_batch": 4, "build_batch": 4, "step_kernel": 1, "build_stage": 1,
+                           "reorder_every": 100}
+    assert {json.loads(k)["reorder_every"] for k in res["trials"]} == {100, -1}
     assert res["ms_per_step"] == pytest.approx(1.0)
     assert res["ms_per_step"] == min(res["trials"].values())
     tried = [json.loads(k) for k in res["trials"]]
@@ -96,11 +98,12 @@ class PhaseSystem(FakeSystem):
         super().__init__()
         self.plan = list(rebuilds_per_trial)
         self.rebuilds = 0
+        self.reorders = 0
         self.timing_on = False
         self.ph = None
 
     def props(self):
-        return [{"rebuilds": self.rebuilds}]
+        return [{"rebuilds": self.rebuilds, "reorders": self.reorders}]
 
     def set_timing(self, on=True):
         self.timing_on = on
@@ -110,7 +113,8 @@ class PhaseSystem(FakeSystem):
         if self.timing_on:
             k = self.plan.pop(0)
             self.rebuilds += k
-            self.ph = {"step": (0.2 * n, n, n), "bin": (0.1 * k, n, n), "reorder": (0.0, 0, 0),
+            self.reorders += 1                  # one reorder of 0.3 ms in each trial
+            self.ph = {"step": (0.2 * n, n, n), "bin": (0.1 * k, n, n), "reorder": (0.3, 1, 1),
                        "build": (0.9 * k, n, n), "props": (0.0, 0, 0), "other": (0.0, 0, 0)}
 
     def timing(self):
@@ -121,11 +125,17 @@ def test_score_does_not_depend_on_the_rebuilds_that_fell_in_a_trial():
     # the same shape timed twice, with 9 and then 14 rebuilds falling into the 100 timed steps:
     # the score is step time + time per rebuild x the rebuild rate over the search, so the
     # second trial scores the same shape no worse than the first
+    # (reorders every 100 steps: 0.3 ms x 1/100 per step)
     s = PhaseSystem([9, 14])
     rate = tune._Rate()
     a = tune._time_steps(s, 100, rate)
     b = tune._time_steps(s, 100, rate)
-    assert a == pytest.approx(0.2 + 1.0 * 9 / 100)
-    assert b == pytest.approx(0.2 + 1.0 * 23 / 200)
+    assert a == pytest.approx(0.2 + 1.0 * 9 / 100 + 0.003)
+    assert b == pytest.approx(0.2 + 1.0 * 23 / 200 + 0.003)
+    # at every rebuild (-1) the same reorder costs 0.3 ms x the rebuild rate
+    s.t["reorder_every"] = -1
+    s.plan = [10]
+    c = tune._time_steps(s, 100, rate)
+    assert c == pytest.approx(0.2 + 1.0 * 33 / 300 + 0.3 * 33 / 300)
     # whole-step timing would have scored the second trial 0.05 ms worse
     assert abs(b - a) < 0.05
