@@ -1063,7 +1063,6 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
 {
     if (!A.g->any_rebuild) return;
     __shared__ float4 s_p[CW_WARPS][2][CW_ROW];
-    __shared__ int32_t s_j[CW_WARPS][2][CW_ROW];
     const float4* __restrict__ ps = A.psort;
     const float rl2 = S.rl2f;
     const float skip2 = rl2 * (1.0f + 1e-5f);
@@ -1126,26 +1125,19 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
                 }
             };
             CwRow cur_row, nxt_row;
-            int32_t rj[CW_PER_LANE];
-            float4 rp[CW_PER_LANE];
+            float4 rp[CW_PER_LANE];                 // a candidate's slot is in .w
             auto load_regs = [&](const CwRow& Q, int q0) {
 #pragma unroll
                 for (int u = 0; u < CW_PER_LANE; ++u) {
                     const int q = q0 + lane + 32 * u;
-                    if (q < Q.tot) {
-                        rp[u] = ps[cw_index(Q, q)];
-                        rj[u] = __float_as_int(rp[u].w);
-                    }
+                    if (q < Q.tot) rp[u] = ps[cw_index(Q, q)];
                 }
             };
             auto store_regs = [&](const CwRow& Q, int q0, int buf) {
 #pragma unroll
                 for (int u = 0; u < CW_PER_LANE; ++u) {
                     const int q = lane + 32 * u;
-                    if (q0 + q < Q.tot) {
-                        s_p[wl][buf][q] = rp[u];
-                        s_j[wl][buf][q] = rj[u];
-                    }
+                    if (q0 + q < Q.tot) s_p[wl][buf][q] = rp[u];
                 }
             };
             auto test_row = [&](const CwRow& Q, int q0, int buf, int rr) {
@@ -1163,7 +1155,7 @@ __global__ void __launch_bounds__(TILE) k_build_cw(Arrays A, Scal S, int cur)
                     const uint32_t code = codeyz | uint32_t(k);
                     for (int q = lo; q < hi; ++q) {
                         const float4 pj = s_p[wl][buf][q - q0];
-                        const int j = s_j[wl][buf][q - q0];
+                        const int j = __float_as_int(pj.w);
                         const float dx = __fadd_rn(__fsub_rn(pj.x, pi.x), offx);
                         const float dy = __fadd_rn(__fsub_rn(pj.y, pi.y), offy);
                         const float dz = __fadd_rn(__fsub_rn(pj.z, pi.z), offz);
